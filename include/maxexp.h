@@ -1,0 +1,158 @@
+/*
+ * maxexp — exponential-integrator Fourier pseudospectral solver for the
+ * periodic 3D Maxwell equations on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the fully discrete scheme of Wang & Jiang, "Time exponential
+ * integrator Fourier pseudospectral methods with high accuracy and multiple
+ * conservation laws for three-dimensional Maxwell's equations"
+ * (arXiv 2210.06232): Def. 2.3, Alg. 1 (initial values: 3D DFT of the six
+ * field components), Alg. 2 (exact per-wavevector exponential of the
+ * spectral curl, Prop. 2.1-2.2, then the inverse 3D DFT), and the discrete
+ * invariants of Sec. 4 (Thm 4.1 energies, Thm 4.3 helicities, Thm 4.4
+ * momenta, Thm 4.6 divergence).
+ *
+ * Conventions shared by every call
+ *  - Every function returns an mx_status and never aborts.  A CUDA error met
+ *    while enqueuing work is returned as MX_E_CUDA and latched in the
+ *    context: every later call on that context returns it again.
+ *  - Field arrays: E and H are each 3 components x [Nz][Ny][Nx] values,
+ *    x fastest (the vector ordering of Sec. 2.2, index
+ *    Nx*Ny*(l-1) + Nx*(k-1) + j), component order (x, y, z).  The element
+ *    type is double for MX_FP64 contexts and float for MX_FP32 contexts.
+ *  - Host pointers are read or written before the call returns.  Device
+ *    pointers are borrowed: the caller keeps ownership and keeps them valid
+ *    until mx_sync returns.  All device work is ordered on the context's
+ *    stream.
+ *  - The library owns every device buffer it allocates and frees it in
+ *    mx_destroy.
+ */
+#ifndef MAXEXP_H
+#define MAXEXP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mx_ctx mx_ctx;
+
+typedef enum {
+  MX_OK = 0,
+  MX_E_INVAL = 1,           /* bad argument (odd N, eps <= 0, non-finite h, NULL pointer, ...) */
+  MX_E_UNSUPPORTED_N = 2,   /* grid size without a compiled FFT plan */
+  MX_E_NOMEM = 3,           /* device allocation failed */
+  MX_E_CUDA = 4,            /* CUDA error (latched) */
+  MX_E_TIMEOUT = 5,         /* a bounded device wait gave up */
+  MX_E_STATE = 6            /* call out of order (e.g. step before load) */
+} mx_status;
+
+typedef enum { MX_FP64 = 0, MX_FP32 = 1 } mx_precision;
+
+/*
+ * Forms of one time step (all compute the same map, Def. 2.3 with
+ * Delta t = h, up to rounding):
+ *  MX_FORM_LITERAL  : the state is the six physical fields; every step runs
+ *                     Alg. 1 step 4 (forward 3D real DFT), Alg. 2 steps 1-4
+ *                     with t_end = h, and Alg. 2 step 5 (inverse 3D DFT).
+ *  MX_FORM_SPECTRAL : the state is the spectrum of the fields at load time
+ *                     (Alg. 1, run once by mx_load_fields); step n writes the
+ *                     spectrum at t_n = n h as R(t_n) applied to it (Alg. 2
+ *                     steps 1-4 with t_end = t_n, phase c|k|t_n taken in
+ *                     FP64).  Physical fields are produced by mx_read_fields
+ *                     (Alg. 2 step 5).
+ */
+typedef enum { MX_FORM_LITERAL = 0, MX_FORM_SPECTRAL = 1 } mx_form;
+
+/*
+ * Discrete invariants of Sec. 4 at one time level.  E3..E6, M1, M2 hold the
+ * k = 1, 2, 3 (x, y, z) members of each family.  divE and divH are the
+ * discrete L2 norms ||D~.(eps E)||_N and ||D~.(mu H)||_N of Thm 4.6, with
+ * <u,v>_N = (1/(Nx Ny Nz)) sum u v.  E5 and E6 vanish identically for real
+ * fields (D_k is antisymmetric) and are returned as 0.  M2 = -M1 exactly
+ * (B_k^T = -B_k).  Helicity H2 is the time-derivative helicity printed with
+ * the label H_1 in Thm 4.3.
+ */
+typedef struct {
+  double t;          /* time of the record */
+  long long step;    /* step index n (0 = load time) */
+  double E1, E2, E3[3], E4[3], E5[3], E6[3];
+  double H1, H2;
+  double M1[3], M2[3];
+  double divE, divH;
+} mx_invariants;
+
+/*
+ * Create a solver context.
+ *  nx, ny, nz : even grid sizes >= 2 (Def. 2.3 Step 1).  Each of nx/2, ny,
+ *               nz must be 2^a, 3*2^a or 5*2^a and at most 512 (ny, nz) or
+ *               256 (nx/2); otherwise MX_E_UNSUPPORTED_N.
+ *  lo, hi     : domain [lo_w, hi_w] per axis (x, y, z), hi_w > lo_w; the
+ *               collocation points are lo_w + (j-1)(hi_w - lo_w)/N_w.
+ *  eps, mu    : permittivity and permeability, positive (eq. maxsys).
+ *  precision  : MX_FP64 or MX_FP32 (arithmetic and storage of the fields;
+ *               phases and invariant sums are FP64 in both).
+ *  form       : MX_FORM_LITERAL or MX_FORM_SPECTRAL.
+ *  stream     : a cudaStream_t to order all work on, or NULL for the
+ *               legacy default stream.
+ * On success *out owns all device memory of the solver (its size is
+ * mx_footprint_bytes); on failure *out is NULL.
+ */
+mx_status mx_create(mx_ctx** out, int nx, int ny, int nz, const double lo[3], const double hi[3], double eps, double mu,
+                    int precision, int form, void* stream);
+
+/* Device bytes a context of this shape would allocate (HBM budgeting). */
+mx_status mx_footprint_bytes(int nx, int ny, int nz, int precision, int form, size_t* bytes);
+
+/*
+ * Load the initial fields E0, H0 at the collocation points (Def. 2.3
+ * Step 2) and run Alg. 1 (forward 3D DFT).  Resets time to 0 and the
+ * invariant record list to the record of t = 0.
+ *  E, H      : 3 x [Nz][Ny][Nx] each, element type of the precision.
+ *  on_device : 0 = host pointers (copied), 1 = device pointers (borrowed
+ *              until mx_sync).
+ */
+mx_status mx_load_fields(mx_ctx* ctx, const void* E, const void* H, int on_device);
+
+/*
+ * Advance nsteps steps of size h (any real h, including negative: the
+ * scheme has no step restriction, Sec. 2.5).  When invariants_every > 0 the
+ * invariants of the state after every step n with n % invariants_every == 0
+ * are appended to the record list; 0 records none.  Work is enqueued on the
+ * context stream; the call does not wait for it.
+ */
+mx_status mx_step(mx_ctx* ctx, double h, long long nsteps, int invariants_every);
+
+/*
+ * Write the fields at the current time (Def. 2.3 Step 4).
+ *  E, H      : 3 x [Nz][Ny][Nx] each, element type of the precision.
+ *  on_device : 0 = host pointers (the call waits for the copy), 1 = device
+ *              pointers (written in stream order; mx_sync to wait).
+ */
+mx_status mx_read_fields(mx_ctx* ctx, void* E, void* H, int on_device);
+
+/*
+ * Copy up to max invariant records (oldest first, starting at load time)
+ * to out; *n_written receives the count.  Waits for the stream.  With
+ * max == 0 nothing is copied (out may be NULL) and *n_written receives the
+ * number of records held.
+ */
+mx_status mx_read_invariants(mx_ctx* ctx, mx_invariants* out, long long max, long long* n_written);
+
+/* Current time and step count of the context. */
+mx_status mx_time(mx_ctx* ctx, double* t, long long* step);
+
+/* Wait for all work of the context; returns a latched error if any. */
+mx_status mx_sync(mx_ctx* ctx);
+
+/* Static description of a status code. */
+const char* mx_strerror(mx_status status);
+
+/* Release the context and all its device memory (NULL is ignored). */
+void mx_destroy(mx_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAXEXP_H */

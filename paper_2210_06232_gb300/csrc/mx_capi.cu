@@ -1,0 +1,480 @@
+// C ABI of libmaxexp: context, plans, device buffers and the step driver.
+// The public contract is documented in include/maxexp.h.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/maxexp.h"
+#include "mx_launch.h"
+
+using mx::GridParams;
+
+struct mx_ctx {
+  int nx, ny, nz, mx;
+  double lo[3], hi[3];
+  double eps, mu;
+  int prec, form;
+  cudaStream_t stream;
+  GridParams g;
+  bool table;  // commensurate |k|^2 -> coefficient table
+  int nq;
+  size_t es, cs;  // real / complex element bytes
+  long long ns, nh;
+  void* phys = nullptr;   // 6 * ns reals: literal state; staging for host I/O
+  void* spec = nullptr;   // 6 * nh complex: literal work spectrum; spectral state at t_n
+  void* spec0 = nullptr;  // spectral form: spectrum at load time
+  void* tab = nullptr;
+  void* twx = nullptr;
+  void* twy = nullptr;
+  void* twz = nullptr;
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  int sblocks;
+  double* rec = nullptr;
+  long long rec_cap = 0, rec_n = 0;
+  std::vector<double> rec_t;
+  std::vector<long long> rec_step;
+  bool loaded = false;
+  bool spec_valid = false;  // spectral form: `spec` holds the state at `t`
+  double t = 0.0;
+  long long step = 0;
+  int tab_kind = -1;
+  double tab_t = NAN;
+  mx_status err = MX_OK;
+};
+
+namespace {
+
+constexpr int REC_STRIDE = 16;  // doubles per invariant record (NSUM used)
+
+bool len_ok(int n) {
+  if (n < 1 || n > 512) return false;
+  int m = n;
+  while (m % 2 == 0) m /= 2;
+  return m == 1 || m == 3 || m == 5;
+}
+
+mx_status cuda_fail(mx_ctx* c, cudaError_t e) {
+  if (e == cudaSuccess) return MX_OK;
+  if (c) c->err = MX_E_CUDA;
+  return MX_E_CUDA;
+}
+
+#define MX_CHECK(c, expr)                                      \
+  do {                                                         \
+    cudaError_t _e = (expr);                                   \
+    if (_e != cudaSuccess) {                                   \
+      if (_e == cudaErrorMemoryAllocation) return MX_E_NOMEM;  \
+      return cuda_fail((c), _e);                               \
+    }                                                          \
+  } while (0)
+
+// exp(-2 pi i j / n) for j < n, reduced to the first quadrant exactly when 4 | n.
+void twiddles(int n, std::vector<double>& re, std::vector<double>& im) {
+  re.resize(n);
+  im.resize(n);
+  for (int j = 0; j < n; ++j) {
+    double c, s;
+    if (n % 4 == 0) {
+      const int q = (4 * j) / n, r = 4 * j - q * n;  // angle = (q + r/n) * pi/2
+      const double a = (M_PI / 2.0) * ((double)r / (double)n);
+      const double ca = cos(a), sa = sin(a);
+      switch (q) {
+        case 0: c = ca; s = sa; break;
+        case 1: c = -sa; s = ca; break;
+        case 2: c = -ca; s = -sa; break;
+        default: c = sa; s = -ca; break;
+      }
+    } else {
+      const double a = 2.0 * M_PI * (double)j / (double)n;
+      c = cos(a);
+      s = sin(a);
+    }
+    re[j] = c;
+    im[j] = -s;
+  }
+}
+
+cudaError_t upload_twiddles(mx_ctx* c, int n, void** dst) {
+  std::vector<double> re, im;
+  twiddles(n, re, im);
+  cudaError_t e = cudaMalloc(dst, (size_t)n * c->cs);
+  if (e != cudaSuccess) return e;
+  if (c->prec == MX_FP64) {
+    std::vector<double2> h(n);
+    for (int j = 0; j < n; ++j) h[j] = make_double2(re[j], im[j]);
+    return cudaMemcpy(*dst, h.data(), n * sizeof(double2), cudaMemcpyHostToDevice);
+  }
+  std::vector<float2> h(n);
+  for (int j = 0; j < n; ++j) h[j] = make_float2((float)re[j], (float)im[j]);
+  return cudaMemcpy(*dst, h.data(), n * sizeof(float2), cudaMemcpyHostToDevice);
+}
+
+// |k|^2 = s0 (a_x m_x^2 + a_y m_y^2 + a_z m_z^2) with small integers a_w when the
+// nu_w^2 are commensurate; q then indexes a table of coefficients.
+bool commensurate(const double nu[3], const int mmax[3], double* s0, int qa[3], int* nq) {
+  double v[3] = {nu[0] * nu[0], nu[1] * nu[1], nu[2] * nu[2]};
+  const double smin = std::min(v[0], std::min(v[1], v[2]));
+  for (int d = 1; d <= 64; ++d) {
+    bool ok = true;
+    long long a[3];
+    for (int w = 0; w < 3; ++w) {
+      const double r = v[w] / smin * d;
+      a[w] = llround(r);
+      if (a[w] < 1 || fabs(r - (double)a[w]) > 1e-12 * r) ok = false;
+    }
+    if (!ok) continue;
+    long long q = 1;
+    for (int w = 0; w < 3; ++w) q += a[w] * (long long)mmax[w] * mmax[w];
+    if (q > (1LL << 24)) return false;
+    *s0 = smin / d;
+    for (int w = 0; w < 3; ++w) qa[w] = (int)a[w];
+    *nq = (int)q;
+    return true;
+  }
+  return false;
+}
+
+int coef_kind(const mx_ctx* c) {
+  // 0 Coef<T> table, 1 CoefHL table, 2 Coef<T> direct, 3 CoefHL direct
+  const bool hl = (c->prec == MX_FP32 && c->form == MX_FORM_LITERAL);
+  return (c->table ? 0 : 2) + (hl ? 1 : 0);
+}
+
+mx_status ensure_records(mx_ctx* c, long long more) {
+  if (c->rec_n + more <= c->rec_cap) return MX_OK;
+  long long cap = std::max<long long>(c->rec_n + more, std::max<long long>(64, 2 * c->rec_cap));
+  double* nr = nullptr;
+  MX_CHECK(c, cudaMalloc(&nr, (size_t)cap * REC_STRIDE * sizeof(double)));
+  if (c->rec && c->rec_n)
+    MX_CHECK(c, cudaMemcpyAsync(nr, c->rec, (size_t)c->rec_n * REC_STRIDE * sizeof(double), cudaMemcpyDeviceToDevice,
+                                c->stream));
+  MX_CHECK(c, cudaStreamSynchronize(c->stream));
+  if (c->rec) cudaFree(c->rec);
+  c->rec = nr;
+  c->rec_cap = cap;
+  return MX_OK;
+}
+
+double* next_record(mx_ctx* c, double t, long long step) {
+  double* r = c->rec + (size_t)c->rec_n * REC_STRIDE;
+  c->rec_t.push_back(t);
+  c->rec_step.push_back(step);
+  ++c->rec_n;
+  return r;
+}
+
+template <typename T> using C2 = mx::cx<T>;
+
+template <typename T>
+cudaError_t forward3(mx_ctx* c, const T* e, const T* h, void* spec) {
+  const long long rows = (long long)c->ny * c->nz;
+  C2<T>* s = (C2<T>*)spec;
+  cudaError_t err = mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const C2<T>*)c->twx, c->stream);
+  if (err != cudaSuccess) return err;
+  err = mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const C2<T>*)c->twy, c->stream);
+  if (err != cudaSuccess) return err;
+  return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const C2<T>*)c->twz, c->stream);
+}
+
+template <typename T>
+cudaError_t inverse3(mx_ctx* c, void* spec, T* e, T* h) {
+  const long long rows = (long long)c->ny * c->nz;
+  C2<T>* s = (C2<T>*)spec;
+  cudaError_t err = mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const C2<T>*)c->twz, c->stream);
+  if (err != cudaSuccess) return err;
+  err = mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const C2<T>*)c->twy, c->stream);
+  if (err != cudaSuccess) return err;
+  const T scale = (T)(1.0 / (double)c->ns);
+  return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const C2<T>*)c->twx, scale, c->stream);
+}
+
+template <typename T>
+cudaError_t ensure_table(mx_ctx* c, double t) {
+  if (!c->table) return cudaSuccess;
+  const int kind = coef_kind(c);
+  if (kind == c->tab_kind && t == c->tab_t) return cudaSuccess;
+  c->tab_kind = kind;
+  c->tab_t = t;
+  return mx::launch_coef_table<T>(kind, c->tab, c->nq, c->g, t, c->stream);
+}
+
+// One spectral pass: dst = R(t) src (mode 1/2) or invariants of src (mode 0).
+template <typename T>
+cudaError_t spectral_pass(mx_ctx* c, int mode, const void* src, void* dst, double t, double* record) {
+  if (mode != 0) {
+    cudaError_t e = ensure_table<T>(c, t);
+    if (e != cudaSuccess) return e;
+  }
+  return mx::launch_spectral<T>(mode, coef_kind(c), (const C2<T>*)src, (C2<T>*)dst, c->nh, c->g, c->tab, t, c->sblocks,
+                                c->partials, c->counter, record, c->stream);
+}
+
+template <typename T>
+mx_status load_t(mx_ctx* c, const void* E, const void* H, int on_device) {
+  const size_t fb = (size_t)3 * c->ns * c->es;
+  const T *e = (const T*)E, *h = (const T*)H;
+  if (!on_device || c->form == MX_FORM_LITERAL) {
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    MX_CHECK(c, cudaMemcpyAsync(c->phys, E, fb, kind, c->stream));
+    MX_CHECK(c, cudaMemcpyAsync((char*)c->phys + fb, H, fb, kind, c->stream));
+    e = (const T*)c->phys;
+    h = (const T*)((const char*)c->phys + fb);
+  }
+  void* target = c->form == MX_FORM_SPECTRAL ? c->spec0 : c->spec;
+  MX_CHECK(c, forward3<T>(c, e, h, target));
+  c->rec_n = 0;
+  c->rec_t.clear();
+  c->rec_step.clear();
+  mx_status st = ensure_records(c, 1);
+  if (st != MX_OK) return st;
+  MX_CHECK(c, spectral_pass<T>(c, 0, target, nullptr, 0.0, next_record(c, 0.0, 0)));
+  if (!on_device) MX_CHECK(c, cudaStreamSynchronize(c->stream));
+  c->t = 0.0;
+  c->step = 0;
+  c->loaded = true;
+  c->spec_valid = false;
+  return MX_OK;
+}
+
+template <typename T>
+mx_status step_t(mx_ctx* c, double h, long long nsteps, int every) {
+  long long nrec = 0;
+  if (every > 0)
+    for (long long i = 1; i <= nsteps; ++i)
+      if ((c->step + i) % every == 0) ++nrec;
+  mx_status st = ensure_records(c, nrec);
+  if (st != MX_OK) return st;
+  const size_t fb = (size_t)3 * c->ns * c->es;
+  const double t0 = c->t;
+  const long long n0 = c->step;
+  for (long long i = 1; i <= nsteps; ++i) {
+    const long long n = n0 + i;
+    const double tn = t0 + (double)i * h;
+    const bool inv = every > 0 && (n % every == 0);
+    double* record = inv ? next_record(c, tn, n) : nullptr;
+    if (c->form == MX_FORM_LITERAL) {
+      T* e = (T*)c->phys;
+      T* hh = (T*)((char*)c->phys + fb);
+      MX_CHECK(c, forward3<T>(c, e, hh, c->spec));
+      MX_CHECK(c, spectral_pass<T>(c, inv ? 2 : 1, c->spec, c->spec, h, record));
+      MX_CHECK(c, inverse3<T>(c, c->spec, e, hh));
+    } else {
+      MX_CHECK(c, spectral_pass<T>(c, inv ? 2 : 1, c->spec0, c->spec, tn, record));
+      c->spec_valid = true;
+    }
+  }
+  c->t = t0 + (double)nsteps * h;
+  c->step = n0 + nsteps;
+  return MX_OK;
+}
+
+template <typename T>
+mx_status read_t(mx_ctx* c, void* E, void* H, int on_device) {
+  const size_t fb = (size_t)3 * c->ns * c->es;
+  if (c->form == MX_FORM_LITERAL) {
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    MX_CHECK(c, cudaMemcpyAsync(E, c->phys, fb, kind, c->stream));
+    MX_CHECK(c, cudaMemcpyAsync(H, (char*)c->phys + fb, fb, kind, c->stream));
+  } else {
+    if (!c->spec_valid) MX_CHECK(c, spectral_pass<T>(c, 1, c->spec0, c->spec, c->t, nullptr));
+    T* e = on_device ? (T*)E : (T*)c->phys;
+    T* h = on_device ? (T*)H : (T*)((char*)c->phys + fb);
+    MX_CHECK(c, inverse3<T>(c, c->spec, e, h));
+    c->spec_valid = false;  // the inverse passes ran in place
+    if (!on_device) {
+      MX_CHECK(c, cudaMemcpyAsync(E, c->phys, fb, cudaMemcpyDeviceToHost, c->stream));
+      MX_CHECK(c, cudaMemcpyAsync(H, (char*)c->phys + fb, fb, cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  if (!on_device) MX_CHECK(c, cudaStreamSynchronize(c->stream));
+  return MX_OK;
+}
+
+size_t footprint(int nx, int ny, int nz, int prec, int form, int nq) {
+  const size_t es = prec == MX_FP64 ? 8 : 4;
+  const size_t ns = (size_t)nx * ny * nz;
+  size_t b = 6 * ns * es;                  // phys
+  b += 6 * ns * es;                        // spec (nh complex == ns reals)
+  if (form == MX_FORM_SPECTRAL) b += 6 * ns * es;  // spec0
+  b += (size_t)nq * 32;                    // table
+  b += (size_t)(nx + ny + nz) * 2 * es;    // twiddles
+  b += (size_t)152 * 4 * 16 * sizeof(double) + 64 * REC_STRIDE * sizeof(double) + 256;
+  return b;
+}
+
+void grid_info(int nx, int ny, int nz, const double lo[3], const double hi[3], double nu[3], int mmax[3]) {
+  for (int w = 0; w < 3; ++w) nu[w] = 2.0 * M_PI / (hi[w] - lo[w]);
+  mmax[0] = nx / 2 - 1;
+  mmax[1] = ny / 2 - 1;
+  mmax[2] = nz / 2 - 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mx_strerror(mx_status s) {
+  switch (s) {
+    case MX_OK: return "ok";
+    case MX_E_INVAL: return "invalid argument";
+    case MX_E_UNSUPPORTED_N: return "unsupported grid size (need even N with N/2 (x) or N (y, z) of the form 2^a, 3*2^a, 5*2^a, <= 512)";
+    case MX_E_NOMEM: return "device allocation failed";
+    case MX_E_CUDA: return "CUDA error";
+    case MX_E_TIMEOUT: return "device wait timed out";
+    case MX_E_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+mx_status mx_footprint_bytes(int nx, int ny, int nz, int precision, int form, size_t* bytes) {
+  if (!bytes || nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2) return MX_E_INVAL;
+  if (precision != MX_FP64 && precision != MX_FP32) return MX_E_INVAL;
+  if (form != MX_FORM_LITERAL && form != MX_FORM_SPECTRAL) return MX_E_INVAL;
+  // worst-case table size for a cubic-cell grid
+  const long long nq = 1 + (long long)(nx / 2 - 1) * (nx / 2 - 1) + (long long)(ny / 2 - 1) * (ny / 2 - 1) +
+                       (long long)(nz / 2 - 1) * (nz / 2 - 1);
+  *bytes = footprint(nx, ny, nz, precision, form, (int)std::min<long long>(nq, 1 << 24));
+  return MX_OK;
+}
+
+mx_status mx_create(mx_ctx** out, int nx, int ny, int nz, const double lo[3], const double hi[3], double eps, double mu,
+                    int precision, int form, void* stream) {
+  if (!out) return MX_E_INVAL;
+  *out = nullptr;
+  if (!lo || !hi) return MX_E_INVAL;
+  if (nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2) return MX_E_INVAL;
+  if (!(eps > 0.0) || !(mu > 0.0) || !isfinite(eps) || !isfinite(mu)) return MX_E_INVAL;
+  for (int w = 0; w < 3; ++w)
+    if (!isfinite(lo[w]) || !isfinite(hi[w]) || !(hi[w] > lo[w])) return MX_E_INVAL;
+  if (precision != MX_FP64 && precision != MX_FP32) return MX_E_INVAL;
+  if (form != MX_FORM_LITERAL && form != MX_FORM_SPECTRAL) return MX_E_INVAL;
+  if (!len_ok(nx / 2) || nx / 2 > 256 || !len_ok(ny) || !len_ok(nz)) return MX_E_UNSUPPORTED_N;
+  if (6LL * nz > 65535) return MX_E_UNSUPPORTED_N;
+
+  mx_ctx* c = new mx_ctx();
+  c->nx = nx; c->ny = ny; c->nz = nz; c->mx = nx / 2;
+  for (int w = 0; w < 3; ++w) { c->lo[w] = lo[w]; c->hi[w] = hi[w]; }
+  c->eps = eps; c->mu = mu; c->prec = precision; c->form = form;
+  c->stream = (cudaStream_t)stream;
+  c->es = precision == MX_FP64 ? 8 : 4;
+  c->cs = 2 * c->es;
+  c->ns = (long long)nx * ny * nz;
+  c->nh = (long long)c->mx * ny * nz;
+  int mmax[3];
+  GridParams& g = c->g;
+  g.nx = nx; g.ny = ny; g.nz = nz; g.mx = c->mx;
+  grid_info(nx, ny, nz, lo, hi, g.nu, mmax);
+  g.eps = eps; g.mu = mu; g.c = 1.0 / sqrt(eps * mu);
+  g.s0 = 0.0; g.qa[0] = g.qa[1] = g.qa[2] = 0;
+  c->nq = 0;
+  c->table = commensurate(g.nu, mmax, &g.s0, g.qa, &c->nq);
+  c->sblocks = mx::spectral_blocks(c->nh);
+
+  auto fail = [&](mx_status s) {
+    mx_destroy(c);
+    return s;
+  };
+  const size_t field_bytes = (size_t)6 * c->ns * c->es;
+  if (cudaMalloc(&c->phys, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (cudaMalloc(&c->spec, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (form == MX_FORM_SPECTRAL && cudaMalloc(&c->spec0, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (c->table && cudaMalloc(&c->tab, (size_t)c->nq * 32) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (cudaMalloc(&c->partials, (size_t)c->sblocks * mx::NSUM * sizeof(double)) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (cudaMalloc(&c->counter, 64) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (cudaMemset(c->counter, 0, 64) != cudaSuccess) return fail(MX_E_CUDA);
+  if (upload_twiddles(c, nx, &c->twx) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (upload_twiddles(c, ny, &c->twy) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (upload_twiddles(c, nz, &c->twz) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (ensure_records(c, 64) != MX_OK) return fail(MX_E_NOMEM);
+  *out = c;
+  return MX_OK;
+}
+
+mx_status mx_load_fields(mx_ctx* c, const void* E, const void* H, int on_device) {
+  if (!c || !E || !H) return MX_E_INVAL;
+  if (c->err != MX_OK) return c->err;
+  return c->prec == MX_FP64 ? load_t<double>(c, E, H, on_device) : load_t<float>(c, E, H, on_device);
+}
+
+mx_status mx_step(mx_ctx* c, double h, long long nsteps, int invariants_every) {
+  if (!c) return MX_E_INVAL;
+  if (c->err != MX_OK) return c->err;
+  if (!isfinite(h) || nsteps < 0 || invariants_every < 0) return MX_E_INVAL;
+  if (!c->loaded) return MX_E_STATE;
+  if (nsteps == 0) return MX_OK;
+  return c->prec == MX_FP64 ? step_t<double>(c, h, nsteps, invariants_every)
+                            : step_t<float>(c, h, nsteps, invariants_every);
+}
+
+mx_status mx_read_fields(mx_ctx* c, void* E, void* H, int on_device) {
+  if (!c || !E || !H) return MX_E_INVAL;
+  if (c->err != MX_OK) return c->err;
+  if (!c->loaded) return MX_E_STATE;
+  return c->prec == MX_FP64 ? read_t<double>(c, E, H, on_device) : read_t<float>(c, E, H, on_device);
+}
+
+mx_status mx_read_invariants(mx_ctx* c, mx_invariants* out, long long max, long long* n_written) {
+  if (!c || !n_written || max < 0 || (max > 0 && !out)) return MX_E_INVAL;
+  if (c->err != MX_OK) return c->err;
+  *n_written = 0;
+  if (max == 0) {
+    *n_written = c->rec_n;
+    return MX_OK;
+  }
+  const long long n = std::min(max, c->rec_n);
+  if (n == 0) return MX_OK;
+  std::vector<double> raw((size_t)n * REC_STRIDE);
+  MX_CHECK(c, cudaMemcpyAsync(raw.data(), c->rec, raw.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MX_CHECK(c, cudaStreamSynchronize(c->stream));
+  const double N = (double)c->ns, N2 = N * N;
+  for (long long i = 0; i < n; ++i) {
+    const double* s = raw.data() + (size_t)i * REC_STRIDE;
+    mx_invariants& r = out[i];
+    memset(&r, 0, sizeof(r));
+    r.t = c->rec_t[i];
+    r.step = c->rec_step[i];
+    r.E1 = s[0] / (2 * N2);
+    r.E2 = s[1] / (2 * N2);
+    for (int w = 0; w < 3; ++w) {
+      r.E3[w] = s[2 + w] / (2 * N2);
+      r.E4[w] = s[5 + w] / (2 * N2);
+      r.M1[w] = -s[10 + w] / N2;
+      r.M2[w] = -r.M1[w];
+    }
+    r.H1 = s[8] / N2;
+    r.H2 = s[9] / N2;
+    r.divE = sqrt(std::max(s[13], 0.0)) / N;
+    r.divH = sqrt(std::max(s[14], 0.0)) / N;
+  }
+  *n_written = n;
+  return MX_OK;
+}
+
+mx_status mx_time(mx_ctx* c, double* t, long long* step) {
+  if (!c) return MX_E_INVAL;
+  if (t) *t = c->t;
+  if (step) *step = c->step;
+  return MX_OK;
+}
+
+mx_status mx_sync(mx_ctx* c) {
+  if (!c) return MX_E_INVAL;
+  if (c->err != MX_OK) return c->err;
+  MX_CHECK(c, cudaStreamSynchronize(c->stream));
+  return MX_OK;
+}
+
+void mx_destroy(mx_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  void* bufs[] = {c->phys, c->spec, c->spec0, c->tab, c->twx, c->twy, c->twz, c->partials, c->counter, c->rec};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete c;
+}
+
+}  // extern "C"

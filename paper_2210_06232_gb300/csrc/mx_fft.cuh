@@ -1,0 +1,194 @@
+// Register-resident mixed-radix (2/3/4/5/8) line FFT for sm_103a.
+//
+// One line of length N is transformed by P = N/E threads, each holding E
+// complex values in registers.  Stage s is a radix-R_s Stockham (autosort)
+// step; every R_s divides E, so a thread performs E/R_s butterflies per stage
+// on values it already holds.  On entry thread t holds x[t + P*m] in v[m]
+// (m = 0..E-1); on exit it holds X[t + P*m] in v[m], natural order.  The
+// same index set is read by the first stage and written by the last one,
+// which lets a forward transform, a per-frequency update and an inverse
+// transform run back to back in registers.  Between stages values are
+// exchanged through a shared-memory line buffer (position p at sm[p*SS]).
+//
+// Transform definition (the paper's Sec. 2.3): forward X_k = sum_j x_j
+// exp(-2 pi i jk/N), inverse without the 1/N factor (callers fold all
+// normalisation into one multiply).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mx {
+
+template <typename T> struct vec2;
+template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+template <typename T> using cx = typename vec2<T>::type;
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return C{a.x * s, a.y * s}; }
+// multiply by (DIR * i): DIR = -1 for the forward kernel exp(-2 pi i / R)
+template <int DIR, typename C> __device__ __forceinline__ C rot(C a) {
+  return DIR < 0 ? C{a.y, -a.x} : C{-a.y, a.x};
+}
+// twiddle w = exp(-2 pi i m / N) stored; the inverse uses its conjugate
+template <int DIR, typename C> __device__ __forceinline__ C twmul(C a, C w) {
+  return DIR < 0 ? cmul(a, w) : cmul(a, cconj(w));
+}
+
+// ---------------------------------------------------------------- butterflies
+// In-register DFT of R values v[0], v[S], ..., v[(R-1)S] (S compile-time stride).
+
+template <int DIR, int S, typename C> __device__ __forceinline__ void bfly2(C* v) {
+  C a = v[0], b = v[S];
+  v[0] = cadd(a, b);
+  v[S] = csub(a, b);
+}
+
+template <int DIR, int S, typename C> __device__ __forceinline__ void bfly4(C* v) {
+  C a = v[0], b = v[S], c = v[2 * S], d = v[3 * S];
+  C s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), d1 = rot<DIR>(csub(b, d));
+  v[0] = cadd(s0, s1);
+  v[S] = cadd(d0, d1);
+  v[2 * S] = csub(s0, s1);
+  v[3 * S] = csub(d0, d1);
+}
+
+template <int DIR, int S, typename C> __device__ __forceinline__ void bfly8(C* v) {
+  using T = decltype(v[0].x);
+  const T h = (T)0.70710678118654752440;  // 1/sqrt(2)
+  C e[4] = {v[0], v[2 * S], v[4 * S], v[6 * S]};
+  C o[4] = {v[S], v[3 * S], v[5 * S], v[7 * S]};
+  bfly4<DIR, 1>(e);
+  bfly4<DIR, 1>(o);
+  // o[k] *= exp(DIR * 2 pi i k / 8)
+  C o1 = o[1], o3 = o[3];
+  o[1] = C{h * (o1.x - DIR * o1.y), h * (o1.y + DIR * o1.x)};
+  o[2] = rot<DIR>(o[2]);
+  o[3] = C{h * (-o3.x - DIR * o3.y), h * (-o3.y + DIR * o3.x)};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k * S] = cadd(e[k], o[k]);
+    v[(k + 4) * S] = csub(e[k], o[k]);
+  }
+}
+
+template <int DIR, int S, typename C> __device__ __forceinline__ void bfly3(C* v) {
+  using T = decltype(v[0].x);
+  const T c1 = (T)-0.5, s1 = (T)0.86602540378443864676;  // cos, sin of 2 pi/3
+  C a = v[0], b = v[S], c = v[2 * S];
+  C s = cadd(b, c), d = csub(b, c);
+  C t = C{a.x + c1 * s.x, a.y + c1 * s.y};
+  C u = rot<DIR>(cscale(d, s1));
+  v[0] = cadd(a, s);
+  v[S] = cadd(t, u);
+  v[2 * S] = csub(t, u);
+}
+
+template <int DIR, int S, typename C> __device__ __forceinline__ void bfly5(C* v) {
+  using T = decltype(v[0].x);
+  const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;  // cos 2pi/5, cos 4pi/5
+  const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;  // sin 2pi/5, sin 4pi/5
+  C a = v[0], b = v[S], c = v[2 * S], d = v[3 * S], e = v[4 * S];
+  C p1 = cadd(b, e), m1 = csub(b, e), p2 = cadd(c, d), m2 = csub(c, d);
+  C t1 = C{a.x + c1 * p1.x + c2 * p2.x, a.y + c1 * p1.y + c2 * p2.y};
+  C t2 = C{a.x + c2 * p1.x + c1 * p2.x, a.y + c2 * p1.y + c1 * p2.y};
+  C u1 = rot<DIR>(C{s1 * m1.x + s2 * m2.x, s1 * m1.y + s2 * m2.y});
+  C u2 = rot<DIR>(C{s2 * m1.x - s1 * m2.x, s2 * m1.y - s1 * m2.y});
+  v[0] = C{a.x + p1.x + p2.x, a.y + p1.y + p2.y};
+  v[S] = cadd(t1, u1);
+  v[4 * S] = csub(t1, u1);
+  v[2 * S] = cadd(t2, u2);
+  v[3 * S] = csub(t2, u2);
+}
+
+template <int R, int DIR, int S, typename C> __device__ __forceinline__ void bfly(C* v) {
+  if constexpr (R == 2) bfly2<DIR, S>(v);
+  else if constexpr (R == 3) bfly3<DIR, S>(v);
+  else if constexpr (R == 4) bfly4<DIR, S>(v);
+  else if constexpr (R == 5) bfly5<DIR, S>(v);
+  else if constexpr (R == 8) bfly8<DIR, S>(v);
+  else static_assert(R == 2, "unsupported radix");
+}
+
+// ------------------------------------------------------------------ planning
+
+// Radix of the next stage: the largest of 8, 5, 4, 3, 2 dividing both the
+// length still to factor and E.
+__host__ __device__ constexpr int pick_radix(int rem, int E) {
+  return (rem % 8 == 0 && E % 8 == 0)   ? 8
+         : (rem % 5 == 0 && E % 5 == 0) ? 5
+         : (rem % 4 == 0 && E % 4 == 0) ? 4
+         : (rem % 3 == 0 && E % 3 == 0) ? 3
+         : (rem % 2 == 0 && E % 2 == 0) ? 2
+                                        : 0;
+}
+__host__ __device__ constexpr bool plan_ok(int N, int E) {
+  if (N <= 0 || E <= 0 || N % E) return false;
+  int rem = N;
+  while (rem > 1) {
+    int r = pick_radix(rem, E);
+    if (!r) return false;
+    rem /= r;
+  }
+  return true;
+}
+__host__ __device__ constexpr int num_stages(int N, int E) {
+  int s = 0, rem = N;
+  while (rem > 1) {
+    rem /= pick_radix(rem, E);
+    ++s;
+  }
+  return s;
+}
+
+// ------------------------------------------------------------------ the line FFT
+//
+// v      : E registers, v[m] <-> position t + P*m
+// sm     : this line's exchange buffer, position p at sm[p * SS]
+// tw     : twiddle table, tw[j * TWS] = exp(-2 pi i j / N) for j < N
+// All threads of the block must call this together (it synchronises).
+template <typename T, int N, int E, int DIR, int NS = 1>
+__device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, const cx<T>* tw, int TWS) {
+  using C = cx<T>;
+  if constexpr (NS < N) {
+    constexpr int P = N / E;
+    constexpr int R = pick_radix(N / NS, E);
+    static_assert(R > 0, "no factorisation for this (N, E)");
+    constexpr int B = E / R;  // butterflies per thread
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + P * b;
+      const int k = j % NS;
+      if constexpr (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const int widx = (r * k) * (N / (NS * R));
+          v[b + r * B] = twmul<DIR>(v[b + r * B], tw[widx * TWS]);
+        }
+      }
+      bfly<R, DIR, B>(v + b);
+    }
+    if constexpr (NS * R < N) {
+      __syncthreads();  // previous readers of sm are done
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int j = t + P * b;
+        const int k = j % NS;
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[(base + r * NS) * SS] = v[b + r * B];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = sm[(t + P * m) * SS];
+      line_fft<T, N, E, DIR, NS * R>(v, sm, SS, t, tw, TWS);
+    }
+  }
+}
+
+}  // namespace mx

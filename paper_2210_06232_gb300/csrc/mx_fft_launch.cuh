@@ -1,0 +1,109 @@
+// Launcher bodies for the FFT kernels, instantiated per precision in
+// mx_fft_f32.cu and mx_fft_f64.cu.
+#pragma once
+#include "mx_launch.h"
+
+namespace mx {
+
+// Registers per thread per line: E complex values.
+constexpr int fft_E(int n) {
+  return (n & (n - 1)) == 0 ? (n <= 8 ? n : 8)
+         : (n % 3 == 0)     ? (n == 3 ? 3 : (n == 6 ? 6 : 12))
+                            : (n == 5 ? 5 : (n == 10 ? 10 : 20));
+}
+constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+// Lines per block: ~256 threads per block.
+constexpr int fft_TY(int n) { return clampi(256 / (n / fft_E(n)), 1, 256); }
+constexpr int fft_TX(int n) { return clampi(256 / (n / fft_E(n)), 8, 64); }
+
+#define MX_FOR_EACH_LEN(X) \
+  X(1) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) \
+  X(3) X(6) X(12) X(24) X(48) X(96) X(192) X(384) \
+  X(5) X(10) X(20) X(40) X(80) X(160) X(320)
+
+template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+template <typename T, int M>
+static cudaError_t x_r2c_n(const T* e, const T* h, cx<T>* out, long rows3, long nrows, const cx<T>* tw, cudaStream_t s) {
+  constexpr int E = fft_E(M), TY = fft_TY(M), P = M / E;
+  static_assert(plan_ok(M, E), "plan");
+  const size_t smem = sizeof(cx<T>) * (2 * M + TY * (M + 1));
+  auto k = k_x_r2c<T, M, E, TY>;
+  cudaError_t err = set_smem(k, smem);
+  if (err != cudaSuccess) return err;
+  const long blocks = (nrows + TY - 1) / TY;
+  k<<<(unsigned)blocks, P * TY, smem, s>>>(e, h, out, rows3, nrows, tw);
+  return cudaGetLastError();
+}
+
+template <typename T, int M>
+static cudaError_t x_c2r_n(const cx<T>* in, T* e, T* h, long rows3, long nrows, const cx<T>* tw, T scale, cudaStream_t s) {
+  constexpr int E = fft_E(M), TY = fft_TY(M), P = M / E;
+  const size_t smem = sizeof(cx<T>) * (2 * M + TY * (M + 1));
+  auto k = k_x_c2r<T, M, E, TY>;
+  cudaError_t err = set_smem(k, smem);
+  if (err != cudaSuccess) return err;
+  const long blocks = (nrows + TY - 1) / TY;
+  k<<<(unsigned)blocks, P * TY, smem, s>>>(in, e, h, rows3, nrows, tw, scale);
+  return cudaGetLastError();
+}
+
+template <typename T, int N, int DIR>
+static cudaError_t strided_n(cx<T>* data, long inner, long outer, const cx<T>* tw, cudaStream_t s) {
+  constexpr int E = fft_E(N), TX = fft_TX(N), P = N / E;
+  static_assert(plan_ok(N, E), "plan");
+  const size_t smem = sizeof(cx<T>) * (N + N * TX);
+  auto k = k_fft_strided<T, N, E, TX, DIR>;
+  cudaError_t err = set_smem(k, smem);
+  if (err != cudaSuccess) return err;
+  const long bx = (inner + TX - 1) / TX;
+  if (bx > 0x7fffffffL || outer > 65535) return cudaErrorInvalidConfiguration;
+  k<<<dim3((unsigned)bx, (unsigned)outer), P * TX, smem, s>>>(data, inner, tw);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_x_r2c(int M, const T* e, const T* h, cx<T>* out, long rows3, long nrows, const cx<T>* tw, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  switch (M) {
+#define X(n) case n: return x_r2c_n<T, n>(e, h, out, rows3, nrows, tw, s);
+    MX_FOR_EACH_LEN(X)
+#undef X
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_x_c2r(int M, const cx<T>* in, T* e, T* h, long rows3, long nrows, const cx<T>* tw, T scale, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  switch (M) {
+#define X(n) case n: return x_c2r_n<T, n>(in, e, h, rows3, nrows, tw, scale, s);
+    MX_FOR_EACH_LEN(X)
+#undef X
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const cx<T>* tw, cudaStream_t s) {
+  if (inner <= 0 || outer <= 0 || N == 1) return cudaSuccess;
+  if (dir < 0) {
+    switch (N) {
+#define X(n) case n: return strided_n<T, n, -1>(data, inner, outer, tw, s);
+      MX_FOR_EACH_LEN(X)
+#undef X
+    }
+  } else {
+    switch (N) {
+#define X(n) case n: return strided_n<T, n, +1>(data, inner, outer, tw, s);
+      MX_FOR_EACH_LEN(X)
+#undef X
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mx

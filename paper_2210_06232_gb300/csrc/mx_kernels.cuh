@@ -1,0 +1,465 @@
+// CUDA kernels of the exponential-integrator Fourier pseudospectral step
+// (Wang & Jiang, arXiv 2210.06232, Alg. 1 and Alg. 2) for sm_103a.
+//
+// Data layout in HBM
+//   physical fields : 6 components (E_x, E_y, E_z, H_x, H_y, H_z), each
+//                     [Nz][Ny][Nx] real, x fastest (the paper's ordering).
+//   spectrum        : 6 components, each [Nz][Ny][Mx] complex, Mx = Nx/2.
+//                     Column kx = 0 is "packed": its real part carries the
+//                     kx = 0 plane and its imaginary part the kx = Nx/2
+//                     (Nyquist) plane.  Both planes have wavenumber k_x = 0
+//                     in the scheme (the Nyquist entry of Omega_x is 0,
+//                     Sec. 2.3), both are transforms of real rows, and the
+//                     per-k update commutes with the packing (it is the
+//                     same real-linear map on both planes and preserves
+//                     Hermitian symmetry), so the y/z transforms, the update
+//                     and the invariant sums act on the packed column as on
+//                     any other.  The spectrum therefore holds exactly as
+//                     many reals as the physical fields.
+#pragma once
+#include "mx_fft.cuh"
+
+namespace mx {
+
+// Grid description shared by all kernels.
+struct GridParams {
+  int nx, ny, nz, mx;   // mx = nx / 2
+  double nu[3];         // nu_w = 2 pi / (w_R - w_L)
+  int qa[3];            // |k|^2 = s0 * (qa0 mx^2 + qa1 my^2 + qa2 mz^2) when commensurate
+  double s0;
+  double eps, mu;
+  double c;             // 1 / sqrt(eps mu)
+};
+
+// Per-|k|^2 coefficients of the exact exponential (Prop. 2.1-2.2 rewritten
+// with k rather than k/|k|):
+//   H' = cos(th) H + al (k.H) k - i bh (k x E)
+//   E' = cos(th) E + al (k.E) k + i be (k x H)
+// th = c |k| t, al = (1 - cos th)/|k|^2, bh = sin(th)/|k| sqrt(eps/mu),
+// be = sin(th)/|k| sqrt(mu/eps).  At k = 0: (1, 0, 0, 0), the identity.
+template <typename T> struct Coef { T c, al, bh, be; };
+// Double-single coefficients (value = hi + lo) for the repeated-step FP32
+// form: the same map is applied every step, so a rounded coefficient would
+// bias every step the same way.
+struct CoefHL { float c, c_l, al, al_l, bh, bh_l, be, be_l; };
+
+__device__ __forceinline__ int signed_index(int i, int n) {
+  // DFT bin -> wavenumber index, Nyquist bin mapped to 0 (Omega_w, Sec. 2.3)
+  return (i < n / 2) ? i : ((i == n / 2) ? 0 : i - n);
+}
+
+// Number of accumulated invariant sums per record.
+constexpr int NSUM = 15;
+
+// --------------------------------------------------------- per-point update
+
+template <typename T, typename CoefT> struct Apply;
+
+template <typename T> struct Apply<T, Coef<T>> {
+  __device__ __forceinline__ static void run(const Coef<T>& q, T kx, T ky, T kz, cx<T>* h, cx<T>* e) {
+    using C = cx<T>;
+    C kh = C{kx * h[0].x + ky * h[1].x + kz * h[2].x, kx * h[0].y + ky * h[1].y + kz * h[2].y};
+    C ke = C{kx * e[0].x + ky * e[1].x + kz * e[2].x, kx * e[0].y + ky * e[1].y + kz * e[2].y};
+    C kxe[3] = {C{ky * e[2].x - kz * e[1].x, ky * e[2].y - kz * e[1].y},
+                C{kz * e[0].x - kx * e[2].x, kz * e[0].y - kx * e[2].y},
+                C{kx * e[1].x - ky * e[0].x, kx * e[1].y - ky * e[0].y}};
+    C kxh[3] = {C{ky * h[2].x - kz * h[1].x, ky * h[2].y - kz * h[1].y},
+                C{kz * h[0].x - kx * h[2].x, kz * h[0].y - kx * h[2].y},
+                C{kx * h[1].x - ky * h[0].x, kx * h[1].y - ky * h[0].y}};
+    const T kv[3] = {kx, ky, kz};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const T ak = q.al * kv[i];
+      // -i * bh * kxe = (bh * kxe.y, -bh * kxe.x)
+      h[i] = C{q.c * h[i].x + ak * kh.x + q.bh * kxe[i].y, q.c * h[i].y + ak * kh.y - q.bh * kxe[i].x};
+      // +i * be * kxh = (-be * kxh.y, be * kxh.x)
+      e[i] = C{q.c * e[i].x + ak * ke.x - q.be * kxh[i].y, q.c * e[i].y + ak * ke.y + q.be * kxh[i].x};
+    }
+  }
+};
+
+template <> struct Apply<float, CoefHL> {
+  __device__ __forceinline__ static void run(const CoefHL& q, float kx, float ky, float kz, float2* h, float2* e) {
+    using C = float2;
+    C kh = C{kx * h[0].x + ky * h[1].x + kz * h[2].x, kx * h[0].y + ky * h[1].y + kz * h[2].y};
+    C ke = C{kx * e[0].x + ky * e[1].x + kz * e[2].x, kx * e[0].y + ky * e[1].y + kz * e[2].y};
+    C kxe[3] = {C{ky * e[2].x - kz * e[1].x, ky * e[2].y - kz * e[1].y},
+                C{kz * e[0].x - kx * e[2].x, kz * e[0].y - kx * e[2].y},
+                C{kx * e[1].x - ky * e[0].x, kx * e[1].y - ky * e[0].y}};
+    C kxh[3] = {C{ky * h[2].x - kz * h[1].x, ky * h[2].y - kz * h[1].y},
+                C{kz * h[0].x - kx * h[2].x, kz * h[0].y - kx * h[2].y},
+                C{kx * h[1].x - ky * h[0].x, kx * h[1].y - ky * h[0].y}};
+    const float kv[3] = {kx, ky, kz};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      // small corrections first, then the leading products
+      const float akh = q.al * kv[i], akl = q.al_l * kv[i];
+      float hx = q.c_l * h[i].x + akl * kh.x + q.bh_l * kxe[i].y;
+      float hy = q.c_l * h[i].y + akl * kh.y - q.bh_l * kxe[i].x;
+      hx = fmaf(q.c, h[i].x, fmaf(akh, kh.x, fmaf(q.bh, kxe[i].y, hx)));
+      hy = fmaf(q.c, h[i].y, fmaf(akh, kh.y, fmaf(-q.bh, kxe[i].x, hy)));
+      float ex = q.c_l * e[i].x + akl * ke.x - q.be_l * kxh[i].y;
+      float ey = q.c_l * e[i].y + akl * ke.y + q.be_l * kxh[i].x;
+      ex = fmaf(q.c, e[i].x, fmaf(akh, ke.x, fmaf(-q.be, kxh[i].y, ex)));
+      ey = fmaf(q.c, e[i].y, fmaf(akh, ke.y, fmaf(q.be, kxh[i].x, ey)));
+      h[i] = C{hx, hy};
+      e[i] = C{ex, ey};
+    }
+  }
+};
+
+// Coefficients computed directly (no table): FP64 arithmetic per point.
+template <typename T, typename CoefT> __device__ __forceinline__ CoefT coef_direct(double k2, double t, const GridParams& g);
+template <> __device__ __forceinline__ Coef<float> coef_direct<float, Coef<float>>(double k2, double t, const GridParams& g) {
+  if (k2 == 0.0) return Coef<float>{1.f, 0.f, 0.f, 0.f};
+  double kabs = sqrt(k2), th = g.c * kabs * t, s, c;
+  sincos(th, &s, &c);
+  double sh;
+  sh = sin(0.5 * th);
+  double al = 2.0 * sh * sh / k2, b = s / kabs;
+  return Coef<float>{(float)c, (float)al, (float)(b * sqrt(g.eps / g.mu)), (float)(b * sqrt(g.mu / g.eps))};
+}
+template <> __device__ __forceinline__ Coef<double> coef_direct<double, Coef<double>>(double k2, double t, const GridParams& g) {
+  if (k2 == 0.0) return Coef<double>{1.0, 0.0, 0.0, 0.0};
+  double kabs = sqrt(k2), th = g.c * kabs * t, s, c;
+  sincos(th, &s, &c);
+  double sh = sin(0.5 * th);
+  double al = 2.0 * sh * sh / k2, b = s / kabs;
+  return Coef<double>{c, al, b * sqrt(g.eps / g.mu), b * sqrt(g.mu / g.eps)};
+}
+__device__ __forceinline__ void split_hl(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+template <> __device__ __forceinline__ CoefHL coef_direct<float, CoefHL>(double k2, double t, const GridParams& g) {
+  CoefHL r;
+  if (k2 == 0.0) {
+    r.c = 1.f; r.c_l = r.al = r.al_l = r.bh = r.bh_l = r.be = r.be_l = 0.f;
+    return r;
+  }
+  double kabs = sqrt(k2), th = g.c * kabs * t, s, c;
+  sincos(th, &s, &c);
+  double sh = sin(0.5 * th);
+  double al = 2.0 * sh * sh / k2, b = s / kabs;
+  split_hl(c, r.c, r.c_l);
+  split_hl(al, r.al, r.al_l);
+  split_hl(b * sqrt(g.eps / g.mu), r.bh, r.bh_l);
+  split_hl(b * sqrt(g.mu / g.eps), r.be, r.be_l);
+  return r;
+}
+
+// Table of coefficients for q = 0 .. nq-1, |k|^2 = s0 q, at time t.
+template <typename T, typename CoefT>
+__global__ void k_coef_table(CoefT* __restrict__ tab, int nq, GridParams g, double t) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nq) tab[q] = coef_direct<T, CoefT>(g.s0 * (double)q, t, g);
+}
+
+// ------------------------------------------------------- invariant densities
+//
+// Parseval on the unnormalised DFT: <u, v>_N = (1/N_S^2) sum_k conj(u_k) v_k.
+// Spectral forms of the Sec. 4 invariants (D_w -> i k_w, D -> i k x):
+//   s0  mu|H|^2 + eps|E|^2                       -> E1 = s0/(2 N_S^2)
+//   s1  |k x E|^2/mu + |k x H|^2/eps             -> E2 = s1/(2 N_S^2)
+//   s2+w  k_w^2 * s0-density                     -> E3[w]
+//   s5+w  k_w^2 * s1-density                     -> E4[w]
+//   s8  k.(Re H x Im H)/eps + k.(Re E x Im E)/mu -> H1 = s8/N_S^2
+//   s9  k.(Re w x Im w)/(eps mu^2) + k.(Re v x Im v)/(mu eps^2),
+//       w = k x E, v = k x H                     -> H2 = s9/N_S^2
+//   s10+w k_w Im(conj(H).E)                      -> M1[w] = -s/N_S^2, M2 = -M1
+//   s13 eps^2 |k.E|^2,  s14 mu^2 |k.H|^2         -> ||div||_N = sqrt(s)/N_S
+// Each density is multiplied by the Hermitian weight of its half-spectrum
+// column (1 for the packed column 0, 2 otherwise).
+template <typename T>
+__device__ __forceinline__ void add_densities(T* acc, T w, T kx, T ky, T kz, const cx<T>* h, const cx<T>* e, T eps, T mu) {
+  using C = cx<T>;
+  const T h2 = h[0].x * h[0].x + h[0].y * h[0].y + h[1].x * h[1].x + h[1].y * h[1].y + h[2].x * h[2].x + h[2].y * h[2].y;
+  const T e2 = e[0].x * e[0].x + e[0].y * e[0].y + e[1].x * e[1].x + e[1].y * e[1].y + e[2].x * e[2].x + e[2].y * e[2].y;
+  C we[3] = {C{ky * e[2].x - kz * e[1].x, ky * e[2].y - kz * e[1].y},
+             C{kz * e[0].x - kx * e[2].x, kz * e[0].y - kx * e[2].y},
+             C{kx * e[1].x - ky * e[0].x, kx * e[1].y - ky * e[0].y}};
+  C vh[3] = {C{ky * h[2].x - kz * h[1].x, ky * h[2].y - kz * h[1].y},
+             C{kz * h[0].x - kx * h[2].x, kz * h[0].y - kx * h[2].y},
+             C{kx * h[1].x - ky * h[0].x, kx * h[1].y - ky * h[0].y}};
+  const T w2 = we[0].x * we[0].x + we[0].y * we[0].y + we[1].x * we[1].x + we[1].y * we[1].y + we[2].x * we[2].x + we[2].y * we[2].y;
+  const T v2 = vh[0].x * vh[0].x + vh[0].y * vh[0].y + vh[1].x * vh[1].x + vh[1].y * vh[1].y + vh[2].x * vh[2].x + vh[2].y * vh[2].y;
+  const T d0 = w * (mu * h2 + eps * e2);
+  const T d1 = w * (w2 / mu + v2 / eps);
+  // k . (a x b) for a = Re, b = Im
+  auto kcross = [&](const C* a) -> T {
+    return kx * (a[1].x * a[2].y - a[2].x * a[1].y) + ky * (a[2].x * a[0].y - a[0].x * a[2].y) +
+           kz * (a[0].x * a[1].y - a[1].x * a[0].y);
+  };
+  const T hel1 = w * (kcross(h) / eps + kcross(e) / mu);
+  const T hel2 = w * (kcross(we) / (eps * mu * mu) + kcross(vh) / (mu * eps * eps));
+  const T mim = w * (h[0].x * e[0].y - h[0].y * e[0].x + h[1].x * e[1].y - h[1].y * e[1].x + h[2].x * e[2].y - h[2].y * e[2].x);
+  const C kE = C{kx * e[0].x + ky * e[1].x + kz * e[2].x, kx * e[0].y + ky * e[1].y + kz * e[2].y};
+  const C kH = C{kx * h[0].x + ky * h[1].x + kz * h[2].x, kx * h[0].y + ky * h[1].y + kz * h[2].y};
+  acc[0] += d0;
+  acc[1] += d1;
+  acc[2] += kx * kx * d0;
+  acc[3] += ky * ky * d0;
+  acc[4] += kz * kz * d0;
+  acc[5] += kx * kx * d1;
+  acc[6] += ky * ky * d1;
+  acc[7] += kz * kz * d1;
+  acc[8] += hel1;
+  acc[9] += hel2;
+  acc[10] += kx * mim;
+  acc[11] += ky * mim;
+  acc[12] += kz * mim;
+  acc[13] += w * eps * eps * (kE.x * kE.x + kE.y * kE.y);
+  acc[14] += w * mu * mu * (kH.x * kH.x + kH.y * kH.y);
+}
+
+// Block-wide FP64 reduction of NSUM values, then a deterministic grid
+// reduction by the last block to finish: partials[block][NSUM] -> record.
+// The counter must be zero on entry; the last block resets it.
+__device__ __forceinline__ void reduce_and_finish(double* acc, double* __restrict__ partials, unsigned* __restrict__ counter,
+                                                  double* __restrict__ record) {
+  __shared__ double red[32][NSUM];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < NSUM; ++i) {
+    double v = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][i] = v;
+  }
+  __syncthreads();
+  const int nblocks = gridDim.x * gridDim.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (threadIdx.x < NSUM) {
+    double v = 0.0;
+    for (int w = 0; w < nwarps; ++w) v += red[w][threadIdx.x];
+    partials[(size_t)bid * NSUM + threadIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(nblocks - 1));
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // fixed order: thread j sums blocks j, j + blockDim.x, ... then a fixed tree
+  double loc[NSUM];
+#pragma unroll
+  for (int i = 0; i < NSUM; ++i) loc[i] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const volatile double* p = partials + (size_t)b * NSUM;
+#pragma unroll
+    for (int i = 0; i < NSUM; ++i) loc[i] += p[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NSUM; ++i) {
+    double v = loc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NSUM) {
+    double v = 0.0;
+    for (int w = 0; w < nwarps; ++w) v += red[w][threadIdx.x];
+    record[threadIdx.x] = v;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// ----------------------------------------------------------------- x passes
+//
+// Real rows of length Nx = 2M -> packed half spectrum of M complex values.
+// z_n = x_{2n} + i x_{2n+1}, Z = DFT_M(z), then for k = 1..M-1
+//   X_k = (Z_k + conj Z_{M-k})/2 + W_N^k (Z_k - conj Z_{M-k})/(2i),
+// and X_0 = Re Z_0 + Im Z_0, X_M = Re Z_0 - Im Z_0 packed as (X_0, X_M).
+// Rows 0 .. 3R-1 come from `in_e`, rows 3R .. 6R-1 from `in_h` (R = Ny Nz).
+template <typename T, int M, int E, int TY>
+__global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in_e, const T* __restrict__ in_h,
+                                                        cx<T>* __restrict__ out, long rows3, long nrows,
+                                                        const cx<T>* __restrict__ twg) {
+  using C = cx<T>;
+  constexpr int P = M / E;
+  constexpr int PITCH = M + 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tw = reinterpret_cast<C*>(smraw);  // 2M entries: exp(-2 pi i j / (2M))
+  C* sm = tw + 2 * M;
+  for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) tw[i] = twg[i];
+  const int t = threadIdx.x % P, ly = threadIdx.x / P;
+  const long row = (long)blockIdx.x * TY + ly;
+  const bool ok = row < nrows;
+  const T* src = ok ? (row < rows3 ? in_e + row * (2L * M) : in_h + (row - rows3) * (2L * M)) : nullptr;
+  C v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int n = t + P * m;
+    v[m] = ok ? *reinterpret_cast<const C*>(src + 2 * n) : C{0, 0};
+  }
+  __syncthreads();  // twiddles
+  C* line = sm + ly * PITCH;
+  line_fft<T, M, E, -1>(v, line, 1, t, tw, 2);
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < E; ++m) line[t + P * m] = v[m];
+  __syncthreads();
+  if (!ok) return;
+  C* dst = out + row * M;
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = t + P * m;
+    C z = line[k];
+    C r;
+    if (k == 0) {
+      r = C{z.x + z.y, z.x - z.y};
+    } else {
+      C zp = cconj(line[M - k]);
+      C a = cadd(z, zp), d = csub(z, zp);   // 2A, 2iB
+      C b = C{d.y, -d.x};                    // 2B = -i * d
+      C wb = cmul(tw[k], b);
+      r = C{(T)0.5 * (a.x + wb.x), (T)0.5 * (a.y + wb.y)};
+    }
+    dst[k] = r;
+  }
+}
+
+// Packed half spectrum -> real rows, scaled by `scale`.
+//   Z'_k = (X_k + conj X_{M-k}) + i conj(W_N^k) (X_k - conj X_{M-k}),
+//   Z'_0 = (X_0 + X_M) + i (X_0 - X_M);  z' = unnormalised IDFT_M(Z') = N z.
+template <typename T, int M, int E, int TY>
+__global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict__ in, T* __restrict__ out_e,
+                                                        T* __restrict__ out_h, long rows3, long nrows,
+                                                        const cx<T>* __restrict__ twg, T scale) {
+  using C = cx<T>;
+  constexpr int P = M / E;
+  constexpr int PITCH = M + 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tw = reinterpret_cast<C*>(smraw);
+  C* sm = tw + 2 * M;
+  for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) tw[i] = twg[i];
+  const int t = threadIdx.x % P, ly = threadIdx.x / P;
+  const long row = (long)blockIdx.x * TY + ly;
+  const bool ok = row < nrows;
+  C* line = sm + ly * PITCH;
+  const C* src = ok ? in + row * M : nullptr;
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = t + P * m;
+    line[k] = ok ? src[k] : C{0, 0};
+  }
+  __syncthreads();
+  C v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = t + P * m;
+    C x = line[k];
+    if (k == 0) {
+      v[m] = C{x.x + x.y, x.x - x.y};
+    } else {
+      C xp = cconj(line[M - k]);
+      C s = cadd(x, xp), d = csub(x, xp);
+      C wd = cmul(cconj(tw[k]), d);
+      v[m] = C{s.x - wd.y, s.y + wd.x};  // s + i * wd
+    }
+  }
+  line_fft<T, M, E, +1>(v, line, 1, t, tw, 2);
+  if (!ok) return;
+  T* dst = row < rows3 ? out_e + row * (2L * M) : out_h + (row - rows3) * (2L * M);
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int n = t + P * m;
+    *reinterpret_cast<C*>(dst + 2 * n) = C{v[m].x * scale, v[m].y * scale};
+  }
+}
+
+// -------------------------------------------------------- strided complex FFT
+//
+// data viewed as [outer][N][inner] complex; transforms every (outer, i)
+// line of N along the middle axis (y: inner = Mx; z: inner = Ny Mx).
+// Block = TX consecutive inner indices x P threads per line.
+template <typename T, int N, int E, int TX, int DIR>
+__global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict__ data, long inner,
+                                                              const cx<T>* __restrict__ twg) {
+  using C = cx<T>;
+  constexpr int P = N / E;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tw = reinterpret_cast<C*>(smraw);
+  C* sm = tw + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  const int x = threadIdx.x % TX, t = threadIdx.x / TX;
+  const long col = (long)blockIdx.x * TX + x;
+  const bool ok = col < inner;
+  C* base = data + (long)blockIdx.y * N * inner + col;
+  C v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = ok ? base[(long)(t + P * m) * inner] : C{0, 0};
+  __syncthreads();
+  line_fft<T, N, E, DIR>(v, sm + x, TX, t, tw, 1);
+  if (!ok) return;
+#pragma unroll
+  for (int m = 0; m < E; ++m) base[(long)(t + P * m) * inner] = v[m];
+}
+
+// ------------------------------------------------------ spectral update pass
+//
+// dst = R(t) src elementwise over the half spectrum (src may equal dst);
+// UPDATE = false reads only (invariants of src).  Grid-stride over points,
+// x fastest; invariants of the written state when INV.
+template <typename T, typename CoefT, bool TABLE, bool UPDATE, bool INV>
+__global__ void __launch_bounds__(256) k_spectral(const cx<T>* __restrict__ src, cx<T>* __restrict__ dst, long comp_stride,
+                                                  GridParams g, const CoefT* __restrict__ tab, double t,
+                                                  double* __restrict__ partials, unsigned* __restrict__ counter,
+                                                  double* __restrict__ record) {
+  using C = cx<T>;
+  const long npts = comp_stride;
+  const int mx = g.mx, ny = g.ny, nz = g.nz;
+  double acc[NSUM];
+  T part[NSUM];
+#pragma unroll
+  for (int i = 0; i < NSUM; ++i) acc[i] = 0.0, part[i] = (T)0;
+  int cnt = 0;
+  const T eps = (T)g.eps, mu = (T)g.mu;
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += (long)gridDim.x * blockDim.x) {
+    const int x = (int)(p % mx);
+    const long r = p / mx;
+    const int y = (int)(r % ny), z = (int)(r / ny);
+    const int my = signed_index(y, ny), mz = signed_index(z, nz);
+    const T kx = (T)(g.nu[0] * x), ky = (T)(g.nu[1] * my), kz = (T)(g.nu[2] * mz);
+    C h[3], e[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      e[c] = src[c * comp_stride + p];
+      h[c] = src[(c + 3) * comp_stride + p];
+    }
+    if constexpr (UPDATE) {
+      CoefT q;
+      if constexpr (TABLE) {
+        const int qi = g.qa[0] * x * x + g.qa[1] * my * my + g.qa[2] * mz * mz;
+        q = tab[qi];
+      } else {
+        const double k2 = g.nu[0] * g.nu[0] * x * x + g.nu[1] * g.nu[1] * (double)my * my + g.nu[2] * g.nu[2] * (double)mz * mz;
+        q = coef_direct<T, CoefT>(k2, t, g);
+      }
+      Apply<T, CoefT>::run(q, kx, ky, kz, h, e);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dst[c * comp_stride + p] = e[c];
+        dst[(c + 3) * comp_stride + p] = h[c];
+      }
+    }
+    if constexpr (INV) {
+      add_densities<T>(part, x == 0 ? (T)1 : (T)2, kx, ky, kz, h, e, eps, mu);
+      if (++cnt == 32) {
+#pragma unroll
+        for (int i = 0; i < NSUM; ++i) acc[i] += (double)part[i], part[i] = (T)0;
+        cnt = 0;
+      }
+    }
+  }
+  if constexpr (INV) {
+#pragma unroll
+    for (int i = 0; i < NSUM; ++i) acc[i] += (double)part[i];
+    reduce_and_finish(acc, partials, counter, record);
+  }
+}
+
+}  // namespace mx

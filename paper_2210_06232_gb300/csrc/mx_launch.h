@@ -1,0 +1,37 @@
+// Host-side launchers of the CUDA kernels (internal to libmaxexp).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mx_kernels.cuh"
+
+namespace mx {
+
+// FFT lengths with a compiled plan: 2^a (1..512), 3*2^a (3..384), 5*2^a (5..320).
+bool fft_len_supported(int n);
+
+template <typename T>
+cudaError_t launch_x_r2c(int M, const T* in_e, const T* in_h, cx<T>* out, long rows3, long nrows, const cx<T>* tw,
+                         cudaStream_t s);
+template <typename T>
+cudaError_t launch_x_c2r(int M, const cx<T>* in, T* out_e, T* out_h, long rows3, long nrows, const cx<T>* tw, T scale,
+                         cudaStream_t s);
+// dir = -1 forward, +1 inverse (unnormalised)
+template <typename T>
+cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const cx<T>* tw, cudaStream_t s);
+
+// Spectral pass.  mode: 0 = invariants only, 1 = update only, 2 = update + invariants.
+// coef_kind: 0 = Coef<T> table, 1 = CoefHL table (float only), 2 = direct Coef<T>, 3 = direct CoefHL.
+template <typename T>
+cudaError_t launch_spectral(int mode, int coef_kind, const cx<T>* src, cx<T>* dst, long npts, const GridParams& g,
+                            const void* tab, double t, int blocks, double* partials, unsigned* counter, double* record,
+                            cudaStream_t s);
+// Fill a coefficient table (coef_kind 0 or 1) for time t.
+template <typename T>
+cudaError_t launch_coef_table(int coef_kind, void* tab, int nq, const GridParams& g, double t, cudaStream_t s);
+
+// Blocks used by the spectral pass for npts points (fixed per size: makes
+// the invariant reduction order independent of what else runs).
+int spectral_blocks(long npts);
+
+}  // namespace mx

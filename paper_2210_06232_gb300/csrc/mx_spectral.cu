@@ -1,0 +1,77 @@
+// Spectral pass (per-k exponential update and invariant sums) and the
+// coefficient-table kernel, instantiated for float and double.
+#include "mx_launch.h"
+
+namespace mx {
+
+int spectral_blocks(long npts) {
+  // persistent-style grid: at most 4 blocks of 256 threads per SM of a 152-SM GB300
+  long b = (npts + 255) / 256;
+  const long cap = 152L * 4L;
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+template <typename T, typename CoefT, bool TABLE>
+static cudaError_t spectral_mode(int mode, const cx<T>* src, cx<T>* dst, long npts, const GridParams& g, const void* tab,
+                                 double t, int blocks, double* partials, unsigned* counter, double* record, cudaStream_t s) {
+  const CoefT* tb = reinterpret_cast<const CoefT*>(tab);
+  switch (mode) {
+    case 0:
+      k_spectral<T, CoefT, TABLE, false, true><<<blocks, 256, 0, s>>>(src, dst, npts, g, tb, t, partials, counter, record);
+      break;
+    case 1:
+      k_spectral<T, CoefT, TABLE, true, false><<<blocks, 256, 0, s>>>(src, dst, npts, g, tb, t, partials, counter, record);
+      break;
+    case 2:
+      k_spectral<T, CoefT, TABLE, true, true><<<blocks, 256, 0, s>>>(src, dst, npts, g, tb, t, partials, counter, record);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_spectral<float>(int mode, int coef_kind, const float2* src, float2* dst, long npts, const GridParams& g,
+                                   const void* tab, double t, int blocks, double* partials, unsigned* counter,
+                                   double* record, cudaStream_t s) {
+  switch (coef_kind) {
+    case 0: return spectral_mode<float, Coef<float>, true>(mode, src, dst, npts, g, tab, t, blocks, partials, counter, record, s);
+    case 1: return spectral_mode<float, CoefHL, true>(mode, src, dst, npts, g, tab, t, blocks, partials, counter, record, s);
+    case 2: return spectral_mode<float, Coef<float>, false>(mode, src, dst, npts, g, tab, t, blocks, partials, counter, record, s);
+    case 3: return spectral_mode<float, CoefHL, false>(mode, src, dst, npts, g, tab, t, blocks, partials, counter, record, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <>
+cudaError_t launch_spectral<double>(int mode, int coef_kind, const double2* src, double2* dst, long npts,
+                                    const GridParams& g, const void* tab, double t, int blocks, double* partials,
+                                    unsigned* counter, double* record, cudaStream_t s) {
+  switch (coef_kind) {
+    case 0: return spectral_mode<double, Coef<double>, true>(mode, src, dst, npts, g, tab, t, blocks, partials, counter, record, s);
+    case 2: return spectral_mode<double, Coef<double>, false>(mode, src, dst, npts, g, tab, t, blocks, partials, counter, record, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <>
+cudaError_t launch_coef_table<float>(int coef_kind, void* tab, int nq, const GridParams& g, double t, cudaStream_t s) {
+  const int blocks = (nq + 255) / 256;
+  if (nq <= 0) return cudaSuccess;
+  if (coef_kind == 0) k_coef_table<float, Coef<float>><<<blocks, 256, 0, s>>>((Coef<float>*)tab, nq, g, t);
+  else if (coef_kind == 1) k_coef_table<float, CoefHL><<<blocks, 256, 0, s>>>((CoefHL*)tab, nq, g, t);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_coef_table<double>(int coef_kind, void* tab, int nq, const GridParams& g, double t, cudaStream_t s) {
+  const int blocks = (nq + 255) / 256;
+  if (nq <= 0) return cudaSuccess;
+  if (coef_kind != 0) return cudaErrorInvalidValue;
+  k_coef_table<double, Coef<double>><<<blocks, 256, 0, s>>>((Coef<double>*)tab, nq, g, t);
+  return cudaGetLastError();
+}
+
+}  // namespace mx

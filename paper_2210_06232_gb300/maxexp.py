@@ -1,0 +1,198 @@
+"""ctypes binding of libmaxexp (include/maxexp.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its own name (``mx_create``,
+``mx_load_fields``, ``mx_step``, ...).  ``Solver`` wraps them for torch
+tensors and numpy arrays; it raises on any non-OK status.  There is no CPU
+fallback: importing this module fails loudly when the shared library is
+missing or does not load.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libmaxexp.so")
+
+MX_OK, MX_E_INVAL, MX_E_UNSUPPORTED_N, MX_E_NOMEM, MX_E_CUDA, MX_E_TIMEOUT, MX_E_STATE = range(7)
+MX_FP64, MX_FP32 = 0, 1
+MX_FORM_LITERAL, MX_FORM_SPECTRAL = 0, 1
+
+
+class mx_invariants(C.Structure):
+    _fields_ = [
+        ("t", C.c_double), ("step", C.c_longlong),
+        ("E1", C.c_double), ("E2", C.c_double),
+        ("E3", C.c_double * 3), ("E4", C.c_double * 3), ("E5", C.c_double * 3), ("E6", C.c_double * 3),
+        ("H1", C.c_double), ("H2", C.c_double),
+        ("M1", C.c_double * 3), ("M2", C.c_double * 3),
+        ("divE", C.c_double), ("divH", C.c_double),
+    ]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = np.array(list(v)) if isinstance(v, C.Array) else v
+        return d
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmaxexp.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                          "python paper_2210_06232_gb300/build.py")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, LL, V = C.c_void_p, C.c_int, C.c_double, C.c_longlong, C.c_void_p
+    D3 = C.POINTER(C.c_double)
+    sig = {
+        "mx_create": (I, [C.POINTER(P), I, I, I, D3, D3, D, D, I, I, V]),
+        "mx_footprint_bytes": (I, [I, I, I, I, I, C.POINTER(C.c_size_t)]),
+        "mx_load_fields": (I, [P, V, V, I]),
+        "mx_step": (I, [P, D, LL, I]),
+        "mx_read_fields": (I, [P, V, V, I]),
+        "mx_read_invariants": (I, [P, C.POINTER(mx_invariants), LL, C.POINTER(LL)]),
+        "mx_time": (I, [P, C.POINTER(D), C.POINTER(LL)]),
+        "mx_sync": (I, [P]),
+        "mx_strerror": (C.c_char_p, [I]),
+        "mx_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib, sig
+
+
+_lib, _SIG = _load()
+EXPORTS = tuple(_SIG)
+
+mx_create = _lib.mx_create
+mx_footprint_bytes = _lib.mx_footprint_bytes
+mx_load_fields = _lib.mx_load_fields
+mx_step = _lib.mx_step
+mx_read_fields = _lib.mx_read_fields
+mx_read_invariants = _lib.mx_read_invariants
+mx_time = _lib.mx_time
+mx_sync = _lib.mx_sync
+mx_strerror = _lib.mx_strerror
+mx_destroy = _lib.mx_destroy
+
+
+class MaxexpError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {mx_strerror(status).decode()} (status {status})")
+
+
+def check(status, where=""):
+    if status != MX_OK:
+        raise MaxexpError(status, where)
+
+
+def _ptr(a, itemsize=None, count=None):
+    """(address, on_device) of a torch tensor or numpy array (contiguous, checked size)."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        isz, n, addr, dev = a.element_size(), a.numel(), a.data_ptr(), 1 if a.is_cuda else 0
+    else:
+        if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be a C-contiguous numpy array")
+        isz, n, addr, dev = a.itemsize, a.size, a.ctypes.data, 0
+    if itemsize is not None and isz != itemsize:
+        raise ValueError(f"element size {isz} does not match the solver precision ({itemsize} bytes)")
+    if count is not None and n != count:
+        raise ValueError(f"array has {n} elements, expected {count}")
+    return addr, dev
+
+
+def footprint_bytes(n, precision=MX_FP64, form=MX_FORM_LITERAL):
+    out = C.c_size_t(0)
+    check(mx_footprint_bytes(int(n[0]), int(n[1]), int(n[2]), int(precision), int(form), C.byref(out)),
+          "mx_footprint_bytes")
+    return int(out.value)
+
+
+class Solver:
+    """One grid, one (eps, mu), one precision and form: a libmaxexp context."""
+
+    def __init__(self, n, lo, hi, eps, mu, precision=MX_FP64, form=MX_FORM_LITERAL, stream=None):
+        self.n = tuple(int(v) for v in n)
+        self.precision = precision
+        self.form = form
+        self.dtype = np.float64 if precision == MX_FP64 else np.float32
+        lo3 = (C.c_double * 3)(*lo)
+        hi3 = (C.c_double * 3)(*hi)
+        h = C.c_void_p()
+        s = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        check(mx_create(C.byref(h), *self.n, lo3, hi3, float(eps), float(mu), int(precision), int(form), s),
+              "mx_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            mx_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _fields(self, E, H):
+        isz = 8 if self.precision == MX_FP64 else 4
+        cnt = 3 * self.n[0] * self.n[1] * self.n[2]
+        pe, de = _ptr(E, isz, cnt)
+        ph, dh = _ptr(H, isz, cnt)
+        return pe, de, ph, dh
+
+    def load(self, E, H):
+        pe, de, ph, dh = self._fields(E, H)
+        if de != dh:
+            raise ValueError("E and H must both be on the host or both on the device")
+        self._keep = (E, H)
+        check(mx_load_fields(self._h, pe, ph, de), "mx_load_fields")
+
+    def step(self, h, nsteps=1, invariants_every=1):
+        check(mx_step(self._h, float(h), int(nsteps), int(invariants_every)), "mx_step")
+
+    def read(self, E, H):
+        pe, de, ph, dh = self._fields(E, H)
+        if de != dh:
+            raise ValueError("E and H must both be on the host or both on the device")
+        check(mx_read_fields(self._h, pe, ph, de), "mx_read_fields")
+        return E, H
+
+    def read_numpy(self):
+        shape = (3, self.n[2], self.n[1], self.n[0])
+        E = np.empty(shape, self.dtype)
+        H = np.empty(shape, self.dtype)
+        return self.read(E, H)
+
+    def invariants(self, max_records=None):
+        if max_records is None:
+            cnt = C.c_longlong(0)
+            check(mx_read_invariants(self._h, None, 0, C.byref(cnt)), "mx_read_invariants")
+            max_records = cnt.value
+        if max_records == 0:
+            return []
+        buf = (mx_invariants * int(max_records))()
+        n = C.c_longlong(0)
+        check(mx_read_invariants(self._h, buf, int(max_records), C.byref(n)), "mx_read_invariants")
+        return [buf[i].as_dict() for i in range(n.value)]
+
+    def time(self):
+        t = C.c_double(0)
+        s = C.c_longlong(0)
+        check(mx_time(self._h, C.byref(t), C.byref(s)), "mx_time")
+        return t.value, s.value
+
+    def sync(self):
+        check(mx_sync(self._h), "mx_sync")
