@@ -139,6 +139,40 @@ mx_status mx_read_fields(mx_ctx* ctx, void* E, void* H, int on_device);
  */
 mx_status mx_read_invariants(mx_ctx* ctx, mx_invariants* out, long long max, long long* n_written);
 
+/*
+ * Load a seeded random, real, divergence-free initial state directly in
+ * Fourier space (an input generator for large grids, not part of the
+ * scheme): per component complex Gaussian coefficients times
+ * exp(-|k|^2 / (2 sigma^2)), projected perpendicular to k, k = 0 and the
+ * Nyquist planes zero, scaled so each field component has RMS about 1.
+ * E and H are independent.  Resets time and records like mx_load_fields.
+ * The same (seed, sigma, grid) gives the same fields on every device.
+ */
+mx_status mx_load_random_divfree(mx_ctx* ctx, unsigned long long seed, double sigma);
+
+/* Kernel classes timed by mx_profile. */
+typedef enum {
+  MX_K_X_R2C = 0,     /* real rows -> packed half spectrum along x */
+  MX_K_X_C2R = 1,     /* packed half spectrum -> real rows along x */
+  MX_K_Y_FFT = 2,     /* complex DFT along y (forward or inverse) */
+  MX_K_Z_FFT = 3,     /* complex DFT along z (forward or inverse) */
+  MX_K_SPECTRAL = 4,  /* per-k exponential update and/or invariant sums */
+  MX_K_TABLE = 5,     /* per-|k|^2 coefficient table */
+  MX_K_GEN = 6,       /* input generator */
+  MX_K_ZFUSED = 7,    /* z DFT + update + inverse z DFT in one pass */
+  MX_K_COUNT = 8
+} mx_kernel_kind;
+
+/*
+ * Per-kernel timing: with enable != 0, every kernel the context launches is
+ * bracketed by CUDA events on the context stream (clears earlier samples).
+ * mx_profile_read waits for the stream and fills ms[MX_K_COUNT] with the
+ * summed device time and launches[MX_K_COUNT] with the launch counts since
+ * the last read, then clears them.
+ */
+mx_status mx_profile(mx_ctx* ctx, int enable);
+mx_status mx_profile_read(mx_ctx* ctx, double* ms, long long* launches);
+
 /* Current time and step count of the context. */
 mx_status mx_time(mx_ctx* ctx, double* t, long long* step);
 

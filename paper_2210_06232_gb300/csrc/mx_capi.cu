@@ -44,6 +44,11 @@ struct mx_ctx {
   int tab_kind = -1;
   double tab_t = NAN;
   mx_status err = MX_OK;
+  // per-kernel event timing (mx_profile)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_kind;
+  size_t prof_used = 0;
 };
 
 namespace {
@@ -169,14 +174,48 @@ double* next_record(mx_ctx* c, double t, long long step) {
 
 template <typename T> using C2 = mx::cx<T>;
 
+// Event pair around one kernel launch when profiling is on.
+struct ProfScope {
+  mx_ctx* c;
+  size_t slot;
+  bool on;
+  ProfScope(mx_ctx* ctx, int kind) : c(ctx), slot(0), on(ctx->prof_on) {
+    if (!on) return;
+    slot = c->prof_used++;
+    while (c->prof_ev.size() < 2 * c->prof_used) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        on = false;
+        --c->prof_used;
+        return;
+      }
+      c->prof_ev.push_back(e);
+    }
+    if (c->prof_kind.size() < c->prof_used) c->prof_kind.resize(c->prof_used);
+    c->prof_kind[slot] = kind;
+    cudaEventRecord(c->prof_ev[2 * slot], c->stream);
+  }
+  ~ProfScope() {
+    if (on) cudaEventRecord(c->prof_ev[2 * slot + 1], c->stream);
+  }
+};
+
 template <typename T>
 cudaError_t forward3(mx_ctx* c, const T* e, const T* h, void* spec) {
   const long long rows = (long long)c->ny * c->nz;
   C2<T>* s = (C2<T>*)spec;
-  cudaError_t err = mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const C2<T>*)c->twx, c->stream);
+  cudaError_t err;
+  {
+    ProfScope ps(c, MX_K_X_R2C);
+    err = mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const C2<T>*)c->twx, c->stream);
+  }
   if (err != cudaSuccess) return err;
-  err = mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const C2<T>*)c->twy, c->stream);
+  {
+    ProfScope ps(c, MX_K_Y_FFT);
+    err = mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const C2<T>*)c->twy, c->stream);
+  }
   if (err != cudaSuccess) return err;
+  ProfScope ps(c, MX_K_Z_FFT);
   return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const C2<T>*)c->twz, c->stream);
 }
 
@@ -184,11 +223,19 @@ template <typename T>
 cudaError_t inverse3(mx_ctx* c, void* spec, T* e, T* h) {
   const long long rows = (long long)c->ny * c->nz;
   C2<T>* s = (C2<T>*)spec;
-  cudaError_t err = mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const C2<T>*)c->twz, c->stream);
+  cudaError_t err;
+  {
+    ProfScope ps(c, MX_K_Z_FFT);
+    err = mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const C2<T>*)c->twz, c->stream);
+  }
   if (err != cudaSuccess) return err;
-  err = mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const C2<T>*)c->twy, c->stream);
+  {
+    ProfScope ps(c, MX_K_Y_FFT);
+    err = mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const C2<T>*)c->twy, c->stream);
+  }
   if (err != cudaSuccess) return err;
   const T scale = (T)(1.0 / (double)c->ns);
+  ProfScope ps(c, MX_K_X_C2R);
   return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const C2<T>*)c->twx, scale, c->stream);
 }
 
@@ -199,6 +246,7 @@ cudaError_t ensure_table(mx_ctx* c, double t) {
   if (kind == c->tab_kind && t == c->tab_t) return cudaSuccess;
   c->tab_kind = kind;
   c->tab_t = t;
+  ProfScope ps(c, MX_K_TABLE);
   return mx::launch_coef_table<T>(kind, c->tab, c->nq, c->g, t, c->stream);
 }
 
@@ -209,6 +257,7 @@ cudaError_t spectral_pass(mx_ctx* c, int mode, const void* src, void* dst, doubl
     cudaError_t e = ensure_table<T>(c, t);
     if (e != cudaSuccess) return e;
   }
+  ProfScope ps(c, MX_K_SPECTRAL);
   return mx::launch_spectral<T>(mode, coef_kind(c), (const C2<T>*)src, (C2<T>*)dst, c->nh, c->g, c->tab, t, c->sblocks,
                                 c->partials, c->counter, record, c->stream);
 }
@@ -233,6 +282,44 @@ mx_status load_t(mx_ctx* c, const void* E, const void* H, int on_device) {
   if (st != MX_OK) return st;
   MX_CHECK(c, spectral_pass<T>(c, 0, target, nullptr, 0.0, next_record(c, 0.0, 0)));
   if (!on_device) MX_CHECK(c, cudaStreamSynchronize(c->stream));
+  c->t = 0.0;
+  c->step = 0;
+  c->loaded = true;
+  c->spec_valid = false;
+  return MX_OK;
+}
+
+template <typename T>
+mx_status load_random_t(mx_ctx* c, unsigned long long seed, double sigma) {
+  // amplitude so that each field component has RMS ~ 1 on the grid:
+  // rms^2 = amp^2 * (sum_k env_k^2) * E|g|^2 (2) * (2/3 left after projection) / N_S^2,
+  // with sum_k env^2 separable over the three axes.
+  const int n[3] = {c->nx, c->ny, c->nz};
+  double sum = 1.0;
+  for (int w = 0; w < 3; ++w) {
+    double sw = 0.0;
+    for (int m = -n[w] / 2 + 1; m <= n[w] / 2 - 1; ++m) {
+      const double k = c->g.nu[w] * m;
+      sw += exp(-k * k / (sigma * sigma));
+    }
+    sum *= sw;
+  }
+  const double amp = (double)c->ns / sqrt(std::max(sum, 1e-300) * 4.0 / 3.0);
+  void* target = c->form == MX_FORM_SPECTRAL ? c->spec0 : c->spec;
+  {
+    ProfScope ps(c, MX_K_GEN);
+    MX_CHECK(c, mx::launch_gen_divfree<T>((C2<T>*)target, c->nh, c->g, seed, sigma, amp, c->stream));
+  }
+  c->rec_n = 0;
+  c->rec_t.clear();
+  c->rec_step.clear();
+  mx_status st = ensure_records(c, 1);
+  if (st != MX_OK) return st;
+  MX_CHECK(c, spectral_pass<T>(c, 0, target, nullptr, 0.0, next_record(c, 0.0, 0)));
+  if (c->form == MX_FORM_LITERAL) {
+    const size_t fb = (size_t)3 * c->ns * c->es;
+    MX_CHECK(c, inverse3<T>(c, c->spec, (T*)c->phys, (T*)((char*)c->phys + fb)));
+  }
   c->t = 0.0;
   c->step = 0;
   c->loaded = true;
@@ -400,6 +487,38 @@ mx_status mx_load_fields(mx_ctx* c, const void* E, const void* H, int on_device)
   return c->prec == MX_FP64 ? load_t<double>(c, E, H, on_device) : load_t<float>(c, E, H, on_device);
 }
 
+mx_status mx_load_random_divfree(mx_ctx* c, unsigned long long seed, double sigma) {
+  if (!c || !(sigma > 0.0) || !isfinite(sigma)) return MX_E_INVAL;
+  if (c->err != MX_OK) return c->err;
+  return c->prec == MX_FP64 ? load_random_t<double>(c, seed, sigma) : load_random_t<float>(c, seed, sigma);
+}
+
+mx_status mx_profile(mx_ctx* c, int enable) {
+  if (!c) return MX_E_INVAL;
+  if (c->err != MX_OK) return c->err;
+  c->prof_on = enable != 0;
+  c->prof_used = 0;
+  return MX_OK;
+}
+
+mx_status mx_profile_read(mx_ctx* c, double* ms, long long* launches) {
+  if (!c || !ms || !launches) return MX_E_INVAL;
+  if (c->err != MX_OK) return c->err;
+  MX_CHECK(c, cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < MX_K_COUNT; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (size_t i = 0; i < c->prof_used; ++i) {
+    float v = 0.f;
+    MX_CHECK(c, cudaEventElapsedTime(&v, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
+    ms[c->prof_kind[i]] += v;
+    launches[c->prof_kind[i]] += 1;
+  }
+  c->prof_used = 0;
+  return MX_OK;
+}
+
 mx_status mx_step(mx_ctx* c, double h, long long nsteps, int invariants_every) {
   if (!c) return MX_E_INVAL;
   if (c->err != MX_OK) return c->err;
@@ -471,6 +590,7 @@ mx_status mx_sync(mx_ctx* c) {
 void mx_destroy(mx_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   void* bufs[] = {c->phys, c->spec, c->spec0, c->tab, c->twx, c->twy, c->twz, c->partials, c->counter, c->rec};
   for (void* b : bufs)
     if (b) cudaFree(b);

@@ -246,9 +246,9 @@ __device__ __forceinline__ void reduce_and_finish(double* acc, double* __restric
 #pragma unroll
   for (int i = 0; i < NSUM; ++i) loc[i] = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    const volatile double* p = partials + (size_t)b * NSUM;
+    const double* p = partials + (size_t)b * NSUM;
 #pragma unroll
-    for (int i = 0; i < NSUM; ++i) loc[i] += p[i];
+    for (int i = 0; i < NSUM; ++i) loc[i] += __ldcg(p + i);
   }
   __syncthreads();
 #pragma unroll
@@ -402,62 +402,108 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
 // ------------------------------------------------------ spectral update pass
 //
 // dst = R(t) src elementwise over the half spectrum (src may equal dst);
-// UPDATE = false reads only (invariants of src).  Grid-stride over points,
-// x fastest; invariants of the written state when INV.
-template <typename T, typename CoefT, bool TABLE, bool UPDATE, bool INV>
-__global__ void __launch_bounds__(256) k_spectral(const cx<T>* __restrict__ src, cx<T>* __restrict__ dst, long comp_stride,
-                                                  GridParams g, const CoefT* __restrict__ tab, double t,
-                                                  double* __restrict__ partials, unsigned* __restrict__ counter,
-                                                  double* __restrict__ record) {
-  using C = cx<T>;
-  const long npts = comp_stride;
-  const int mx = g.mx, ny = g.ny, nz = g.nz;
-  double acc[NSUM];
-  T part[NSUM];
+// UPDATE = false reads only (invariants of src).  Each thread takes V
+// consecutive points of one row per iteration (V = 2: 16-byte FP32 loads),
+// grid-stride over the flattened [Nz][Ny][Mx] index.  Invariant densities
+// of the written state are summed in T over at most CHUNK iterations, then
+// added into per-thread FP64 slots in shared memory; the block and grid
+// reductions are FP64 (reduce_and_finish).
+template <typename T> struct vec4;
+template <> struct vec4<float> { using type = float4; };
+
+template <typename T, int V>
+__device__ __forceinline__ void load_pts(const cx<T>* __restrict__ a, long i, cx<T>* out) {
+  if constexpr (V == 2 && sizeof(T) == 4) {
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(a + i));
+    out[0] = cx<T>{v.x, v.y};
+    out[1] = cx<T>{v.z, v.w};
+  } else {
 #pragma unroll
-  for (int i = 0; i < NSUM; ++i) acc[i] = 0.0, part[i] = (T)0;
-  int cnt = 0;
+    for (int j = 0; j < V; ++j) out[j] = __ldcs(a + i + j);
+  }
+}
+template <typename T, int V>
+__device__ __forceinline__ void store_pts(cx<T>* __restrict__ a, long i, const cx<T>* in) {
+  if constexpr (V == 2 && sizeof(T) == 4) {
+    __stcs(reinterpret_cast<float4*>(a + i), make_float4(in[0].x, in[0].y, in[1].x, in[1].y));
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) __stcs(a + i + j, in[j]);
+  }
+}
+
+template <typename T, typename CoefT, bool TABLE, bool UPDATE, bool INV, int V>
+__global__ void __launch_bounds__(256, 2) k_spectral(const cx<T>* __restrict__ src, cx<T>* __restrict__ dst,
+                                                     long comp_stride, GridParams g, const CoefT* __restrict__ tab,
+                                                     double t, double* __restrict__ partials,
+                                                     unsigned* __restrict__ counter, double* __restrict__ record) {
+  using C = cx<T>;
+  constexpr int CHUNK = 16;
+  __shared__ double sacc[INV ? NSUM : 1][256];
+  const unsigned npts = (unsigned)comp_stride;
+  const unsigned mx = (unsigned)g.mx, ny = (unsigned)g.ny;
   const T eps = (T)g.eps, mu = (T)g.mu;
-  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += (long)gridDim.x * blockDim.x) {
-    const int x = (int)(p % mx);
-    const long r = p / mx;
-    const int y = (int)(r % ny), z = (int)(r / ny);
-    const int my = signed_index(y, ny), mz = signed_index(z, nz);
-    const T kx = (T)(g.nu[0] * x), ky = (T)(g.nu[1] * my), kz = (T)(g.nu[2] * mz);
-    C h[3], e[3];
+  const T nux = (T)g.nu[0], nuy = (T)g.nu[1], nuz = (T)g.nu[2];
+  T part[INV ? NSUM : 1];
+  if constexpr (INV) {
+#pragma unroll
+    for (int i = 0; i < NSUM; ++i) part[i] = (T)0, sacc[i][threadIdx.x] = 0.0;
+  }
+  int cnt = 0;
+  const unsigned stride = gridDim.x * blockDim.x * V;
+  for (unsigned p = (blockIdx.x * blockDim.x + threadIdx.x) * V; p < npts; p += stride) {
+    const unsigned r = p / mx;
+    const int x0 = (int)(p - r * mx);
+    const unsigned z = r / ny;
+    const int y = (int)(r - z * ny);
+    const int my = signed_index(y, g.ny), mz = signed_index((int)z, g.nz);
+    const T ky = nuy * (T)my, kz = nuz * (T)mz;
+    C e[3][V], h[3][V];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      e[c] = src[c * comp_stride + p];
-      h[c] = src[(c + 3) * comp_stride + p];
+      load_pts<T, V>(src, (long)c * comp_stride + p, e[c]);
+      load_pts<T, V>(src, (long)(c + 3) * comp_stride + p, h[c]);
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const int x = x0 + j;
+      const T kx = nux * (T)x;
+      C hh[3] = {h[0][j], h[1][j], h[2][j]};
+      C ee[3] = {e[0][j], e[1][j], e[2][j]};
+      if constexpr (UPDATE) {
+        CoefT q;
+        if constexpr (TABLE) {
+          q = tab[g.qa[0] * x * x + g.qa[1] * my * my + g.qa[2] * mz * mz];
+        } else {
+          const double k2 = g.nu[0] * g.nu[0] * (double)x * x + g.nu[1] * g.nu[1] * (double)my * my +
+                            g.nu[2] * g.nu[2] * (double)mz * mz;
+          q = coef_direct<T, CoefT>(k2, t, g);
+        }
+        Apply<T, CoefT>::run(q, kx, ky, kz, hh, ee);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[c][j] = hh[c], e[c][j] = ee[c];
+      }
+      if constexpr (INV) add_densities<T>(part, x == 0 ? (T)1 : (T)2, kx, ky, kz, hh, ee, eps, mu);
     }
     if constexpr (UPDATE) {
-      CoefT q;
-      if constexpr (TABLE) {
-        const int qi = g.qa[0] * x * x + g.qa[1] * my * my + g.qa[2] * mz * mz;
-        q = tab[qi];
-      } else {
-        const double k2 = g.nu[0] * g.nu[0] * x * x + g.nu[1] * g.nu[1] * (double)my * my + g.nu[2] * g.nu[2] * (double)mz * mz;
-        q = coef_direct<T, CoefT>(k2, t, g);
-      }
-      Apply<T, CoefT>::run(q, kx, ky, kz, h, e);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        dst[c * comp_stride + p] = e[c];
-        dst[(c + 3) * comp_stride + p] = h[c];
+        store_pts<T, V>(dst, (long)c * comp_stride + p, e[c]);
+        store_pts<T, V>(dst, (long)(c + 3) * comp_stride + p, h[c]);
       }
     }
     if constexpr (INV) {
-      add_densities<T>(part, x == 0 ? (T)1 : (T)2, kx, ky, kz, h, e, eps, mu);
-      if (++cnt == 32) {
+      if (++cnt == CHUNK) {
 #pragma unroll
-        for (int i = 0; i < NSUM; ++i) acc[i] += (double)part[i], part[i] = (T)0;
+        for (int i = 0; i < NSUM; ++i) sacc[i][threadIdx.x] += (double)part[i], part[i] = (T)0;
         cnt = 0;
       }
     }
   }
   if constexpr (INV) {
+    double acc[NSUM];
 #pragma unroll
-    for (int i = 0; i < NSUM; ++i) acc[i] += (double)part[i];
+    for (int i = 0; i < NSUM; ++i) acc[i] = sacc[i][threadIdx.x] + (double)part[i];
     reduce_and_finish(acc, partials, counter, record);
   }
 }

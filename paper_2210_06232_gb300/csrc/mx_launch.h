@@ -30,6 +30,11 @@ cudaError_t launch_spectral(int mode, int coef_kind, const cx<T>* src, cx<T>* ds
 template <typename T>
 cudaError_t launch_coef_table(int coef_kind, void* tab, int nq, const GridParams& g, double t, cudaStream_t s);
 
+// Seeded random divergence-free spectrum (input generator), packed layout.
+template <typename T>
+cudaError_t launch_gen_divfree(cx<T>* spec, long npts, const GridParams& g, unsigned long long seed, double sigma,
+                               double amp, cudaStream_t s);
+
 // Blocks used by the spectral pass for npts points (fixed per size: makes
 // the invariant reduction order independent of what else runs).
 int spectral_blocks(long npts);

@@ -5,30 +5,40 @@
 namespace mx {
 
 int spectral_blocks(long npts) {
-  // persistent-style grid: at most 4 blocks of 256 threads per SM of a 152-SM GB300
-  long b = (npts + 255) / 256;
-  const long cap = 152L * 4L;
+  // persistent-style grid: at most 2 blocks of 256 threads per SM of a 152-SM GB300
+  long b = (npts + 511) / 512;
+  const long cap = 152L * 2L;
   return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
-template <typename T, typename CoefT, bool TABLE>
-static cudaError_t spectral_mode(int mode, const cx<T>* src, cx<T>* dst, long npts, const GridParams& g, const void* tab,
-                                 double t, int blocks, double* partials, unsigned* counter, double* record, cudaStream_t s) {
+template <typename T, typename CoefT, bool TABLE, int V>
+static cudaError_t spectral_v(int mode, const cx<T>* src, cx<T>* dst, long npts, const GridParams& g, const void* tab,
+                              double t, int blocks, double* partials, unsigned* counter, double* record, cudaStream_t s) {
   const CoefT* tb = reinterpret_cast<const CoefT*>(tab);
   switch (mode) {
     case 0:
-      k_spectral<T, CoefT, TABLE, false, true><<<blocks, 256, 0, s>>>(src, dst, npts, g, tb, t, partials, counter, record);
+      k_spectral<T, CoefT, TABLE, false, true, V><<<blocks, 256, 0, s>>>(src, dst, npts, g, tb, t, partials, counter, record);
       break;
     case 1:
-      k_spectral<T, CoefT, TABLE, true, false><<<blocks, 256, 0, s>>>(src, dst, npts, g, tb, t, partials, counter, record);
+      k_spectral<T, CoefT, TABLE, true, false, V><<<blocks, 256, 0, s>>>(src, dst, npts, g, tb, t, partials, counter, record);
       break;
     case 2:
-      k_spectral<T, CoefT, TABLE, true, true><<<blocks, 256, 0, s>>>(src, dst, npts, g, tb, t, partials, counter, record);
+      k_spectral<T, CoefT, TABLE, true, true, V><<<blocks, 256, 0, s>>>(src, dst, npts, g, tb, t, partials, counter, record);
       break;
     default:
       return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <typename T, typename CoefT, bool TABLE>
+static cudaError_t spectral_mode(int mode, const cx<T>* src, cx<T>* dst, long npts, const GridParams& g, const void* tab,
+                                 double t, int blocks, double* partials, unsigned* counter, double* record, cudaStream_t s) {
+  if (npts >= (1L << 31)) return cudaErrorInvalidValue;
+  // two points per thread when rows have even length (keeps both in one row, 16-byte aligned)
+  if (sizeof(T) == 4 && g.mx % 2 == 0)
+    return spectral_v<T, CoefT, TABLE, 2>(mode, src, dst, npts, g, tab, t, blocks, partials, counter, record, s);
+  return spectral_v<T, CoefT, TABLE, 1>(mode, src, dst, npts, g, tab, t, blocks, partials, counter, record, s);
 }
 
 template <>

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libmaxexp.so")
 MX_OK, MX_E_INVAL, MX_E_UNSUPPORTED_N, MX_E_NOMEM, MX_E_CUDA, MX_E_TIMEOUT, MX_E_STATE = range(7)
 MX_FP64, MX_FP32 = 0, 1
 MX_FORM_LITERAL, MX_FORM_SPECTRAL = 0, 1
+KERNEL_KINDS = ("x_r2c", "x_c2r", "y_fft", "z_fft", "spectral", "table", "gen", "z_fused")
 
 
 class mx_invariants(C.Structure):
@@ -54,6 +55,9 @@ def _load():
         "mx_read_fields": (I, [P, V, V, I]),
         "mx_read_invariants": (I, [P, C.POINTER(mx_invariants), LL, C.POINTER(LL)]),
         "mx_time": (I, [P, C.POINTER(D), C.POINTER(LL)]),
+        "mx_load_random_divfree": (I, [P, C.c_ulonglong, D]),
+        "mx_profile": (I, [P, I]),
+        "mx_profile_read": (I, [P, C.POINTER(D), C.POINTER(LL)]),
         "mx_sync": (I, [P]),
         "mx_strerror": (C.c_char_p, [I]),
         "mx_destroy": (None, [P]),
@@ -75,6 +79,9 @@ mx_step = _lib.mx_step
 mx_read_fields = _lib.mx_read_fields
 mx_read_invariants = _lib.mx_read_invariants
 mx_time = _lib.mx_time
+mx_load_random_divfree = _lib.mx_load_random_divfree
+mx_profile = _lib.mx_profile
+mx_profile_read = _lib.mx_profile_read
 mx_sync = _lib.mx_sync
 mx_strerror = _lib.mx_strerror
 mx_destroy = _lib.mx_destroy
@@ -187,6 +194,19 @@ class Solver:
         n = C.c_longlong(0)
         check(mx_read_invariants(self._h, buf, int(max_records), C.byref(n)), "mx_read_invariants")
         return [buf[i].as_dict() for i in range(n.value)]
+
+    def load_random(self, seed, sigma):
+        check(mx_load_random_divfree(self._h, int(seed), float(sigma)), "mx_load_random_divfree")
+
+    def profile(self, enable=True):
+        check(mx_profile(self._h, 1 if enable else 0), "mx_profile")
+
+    def profile_read(self):
+        n = len(KERNEL_KINDS)
+        ms = (C.c_double * n)()
+        cnt = (C.c_longlong * n)()
+        check(mx_profile_read(self._h, ms, cnt), "mx_profile_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
 
     def time(self):
         t = C.c_double(0)
