@@ -173,6 +173,41 @@ typedef enum {
 mx_status mx_profile(mx_ctx* ctx, int enable);
 mx_status mx_profile_read(mx_ctx* ctx, double* ms, long long* launches);
 
+/*
+ * Allocation-free spectral pass.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc (code running inside
+ * another framework's memory pool, code that must not allocate while a
+ * stream is being recorded, embedded hosts that forbid the library from
+ * growing device memory).  It applies the exact exponential R(t) to a
+ * caller-owned packed half spectrum and/or reduces its invariants, without
+ * a context and without allocating anything.
+ *  spec_in   : device, 6 x [nz][ny][nx/2] complex (E_x, E_y, E_z, H_x, H_y,
+ *              H_z; element = 2 x double for MX_FP64, 2 x float for MX_FP32),
+ *              the unnormalised 3D DFT of real fields with column kx = 0
+ *              holding the kx = 0 plane in its real part and the kx = nx/2
+ *              plane in its imaginary part.
+ *  spec_out  : device, same layout; receives R(t) spec_in (may equal
+ *              spec_in).  NULL: no update, invariants of spec_in only.
+ *  inv_out   : host; receives the invariants of the written spectrum (of
+ *              spec_in when spec_out is NULL), t = t, step = 0.  NULL: none.
+ *              When given, the call waits for the stream.
+ *  nx..mu, precision : as for mx_create (any even sizes >= 2).
+ *  stream    : cudaStream_t or NULL.
+ * Device memory: besides spec_in and spec_out the pass uses one static
+ * device array of about 40 KB (partial sums of at most 304 blocks, a block
+ * counter and one record), present on every device that loads the library.
+ * Coefficients are computed per point in FP64 (no table), so the pass is
+ * slower than mx_step.  Errors: MX_E_INVAL for bad arguments,
+ * MX_E_UNSUPPORTED_N when (nx/2) * ny * nz >= 2^31, MX_E_CUDA otherwise.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (concurrent
+ * streams or threads) race and must be serialised by the caller.
+ */
+mx_status mx_spectral_update_noalloc(const void* spec_in, void* spec_out, int nx, int ny, int nz, const double lo[3],
+                                     const double hi[3], double eps, double mu, int precision, double t,
+                                     mx_invariants* inv_out, void* stream);
+
 /* Current time and step count of the context. */
 mx_status mx_time(mx_ctx* ctx, double* t, long long* step);
 

@@ -57,6 +57,7 @@ def _load():
         "mx_time": (I, [P, C.POINTER(D), C.POINTER(LL)]),
         "mx_load_random_divfree": (I, [P, C.c_ulonglong, D]),
         "mx_profile": (I, [P, I]),
+        "mx_spectral_update_noalloc": (I, [V, V, I, I, I, D3, D3, D, D, I, D, C.POINTER(mx_invariants), V]),
         "mx_profile_read": (I, [P, C.POINTER(D), C.POINTER(LL)]),
         "mx_sync": (I, [P]),
         "mx_strerror": (C.c_char_p, [I]),
@@ -81,6 +82,7 @@ mx_read_invariants = _lib.mx_read_invariants
 mx_time = _lib.mx_time
 mx_load_random_divfree = _lib.mx_load_random_divfree
 mx_profile = _lib.mx_profile
+mx_spectral_update_noalloc = _lib.mx_spectral_update_noalloc
 mx_profile_read = _lib.mx_profile_read
 mx_sync = _lib.mx_sync
 mx_strerror = _lib.mx_strerror
