@@ -103,19 +103,25 @@ void twiddles(int n, std::vector<double>& re, std::vector<double>& im) {
   }
 }
 
+// FP64: double2 per entry.  FP32: float4 (hi.x, hi.y, lo.x, lo.y) with value = hi + lo.
 cudaError_t upload_twiddles(mx_ctx* c, int n, void** dst) {
   std::vector<double> re, im;
   twiddles(n, re, im);
-  cudaError_t e = cudaMalloc(dst, (size_t)n * c->cs);
-  if (e != cudaSuccess) return e;
   if (c->prec == MX_FP64) {
+    cudaError_t e = cudaMalloc(dst, (size_t)n * sizeof(double2));
+    if (e != cudaSuccess) return e;
     std::vector<double2> h(n);
     for (int j = 0; j < n; ++j) h[j] = make_double2(re[j], im[j]);
     return cudaMemcpy(*dst, h.data(), n * sizeof(double2), cudaMemcpyHostToDevice);
   }
-  std::vector<float2> h(n);
-  for (int j = 0; j < n; ++j) h[j] = make_float2((float)re[j], (float)im[j]);
-  return cudaMemcpy(*dst, h.data(), n * sizeof(float2), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMalloc(dst, (size_t)n * sizeof(float4));
+  if (e != cudaSuccess) return e;
+  std::vector<float4> h(n);
+  for (int j = 0; j < n; ++j) {
+    const float rh = (float)re[j], ih = (float)im[j];
+    h[j] = make_float4(rh, ih, (float)(re[j] - (double)rh), (float)(im[j] - (double)ih));
+  }
+  return cudaMemcpy(*dst, h.data(), n * sizeof(float4), cudaMemcpyHostToDevice);
 }
 
 // |k|^2 = s0 (a_x m_x^2 + a_y m_y^2 + a_z m_z^2) with small integers a_w when the
@@ -207,16 +213,16 @@ cudaError_t forward3(mx_ctx* c, const T* e, const T* h, void* spec) {
   cudaError_t err;
   {
     ProfScope ps(c, MX_K_X_R2C);
-    err = mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const C2<T>*)c->twx, c->stream);
+    err = mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, c->stream);
   }
   if (err != cudaSuccess) return err;
   {
     ProfScope ps(c, MX_K_Y_FFT);
-    err = mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const C2<T>*)c->twy, c->stream);
+    err = mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, c->stream);
   }
   if (err != cudaSuccess) return err;
   ProfScope ps(c, MX_K_Z_FFT);
-  return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const C2<T>*)c->twz, c->stream);
+  return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, c->stream);
 }
 
 template <typename T>
@@ -226,17 +232,17 @@ cudaError_t inverse3(mx_ctx* c, void* spec, T* e, T* h) {
   cudaError_t err;
   {
     ProfScope ps(c, MX_K_Z_FFT);
-    err = mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const C2<T>*)c->twz, c->stream);
+    err = mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, c->stream);
   }
   if (err != cudaSuccess) return err;
   {
     ProfScope ps(c, MX_K_Y_FFT);
-    err = mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const C2<T>*)c->twy, c->stream);
+    err = mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, c->stream);
   }
   if (err != cudaSuccess) return err;
-  const T scale = (T)(1.0 / (double)c->ns);
+  const double scale = 1.0 / (double)c->ns;
   ProfScope ps(c, MX_K_X_C2R);
-  return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const C2<T>*)c->twx, scale, c->stream);
+  return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, scale, c->stream);
 }
 
 template <typename T>
@@ -584,6 +590,13 @@ mx_status mx_sync(mx_ctx* c) {
   if (!c) return MX_E_INVAL;
   if (c->err != MX_OK) return c->err;
   MX_CHECK(c, cudaStreamSynchronize(c->stream));
+  // counter[1] is set by a kernel whose bounded wait gave up
+  unsigned flag = 0;
+  MX_CHECK(c, cudaMemcpy(&flag, c->counter + 1, sizeof(flag), cudaMemcpyDeviceToHost));
+  if (flag) {
+    c->err = MX_E_TIMEOUT;
+    return c->err;
+  }
   return MX_OK;
 }
 

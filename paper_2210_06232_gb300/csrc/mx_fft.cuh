@@ -24,6 +24,40 @@ template <> struct vec2<float> { using type = float2; };
 template <> struct vec2<double> { using type = double2; };
 template <typename T> using cx = typename vec2<T>::type;
 
+// Twiddle storage: FP64 keeps one double2; FP32 keeps the value as a pair
+// hi + lo of floats (float4: hi.x, hi.y, lo.x, lo.y).  In FP32 every FFT
+// constant is applied as hi + lo: a rounded constant would scale each
+// frequency by the same wrong factor on every transform, and in a repeated
+// forward/inverse loop that bias grows linearly with the step count.
+template <typename T> struct tw_t;
+template <> struct tw_t<float> { using type = float4; };
+template <> struct tw_t<double> { using type = double2; };
+template <typename T> using twv = typename tw_t<T>::type;
+
+// a * w (forward, DIR < 0) or a * conj(w) (inverse)
+template <int DIR> __device__ __forceinline__ double2 twmul(double2 a, double2 w) {
+  const double wy = DIR < 0 ? w.y : -w.y;
+  return double2{a.x * w.x - a.y * wy, a.x * wy + a.y * w.x};
+}
+template <int DIR> __device__ __forceinline__ float2 twmul(float2 a, float4 w) {
+  const float hy = DIR < 0 ? w.y : -w.y, ly = DIR < 0 ? w.w : -w.w;
+  const float re = fmaf(a.x, w.x, fmaf(-a.y, hy, a.x * w.z - a.y * ly));
+  const float im = fmaf(a.x, hy, fmaf(a.y, w.x, a.x * ly + a.y * w.z));
+  return float2{re, im};
+}
+// x * c for a real constant c given in FP64: hi + lo in FP32, plain in FP64
+template <typename T> struct KC;
+template <> struct KC<double> {
+  double v;
+  __device__ __forceinline__ constexpr KC(double c) : v(c) {}
+  __device__ __forceinline__ double mul(double x) const { return x * v; }
+};
+template <> struct KC<float> {
+  float h, l;
+  __device__ __forceinline__ constexpr KC(double c) : h((float)c), l((float)(c - (double)(float)c)) {}
+  __device__ __forceinline__ float mul(float x) const { return fmaf(x, h, x * l); }
+};
+
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
@@ -34,10 +68,6 @@ template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) 
 // multiply by (DIR * i): DIR = -1 for the forward kernel exp(-2 pi i / R)
 template <int DIR, typename C> __device__ __forceinline__ C rot(C a) {
   return DIR < 0 ? C{a.y, -a.x} : C{-a.y, a.x};
-}
-// twiddle w = exp(-2 pi i m / N) stored; the inverse uses its conjugate
-template <int DIR, typename C> __device__ __forceinline__ C twmul(C a, C w) {
-  return DIR < 0 ? cmul(a, w) : cmul(a, cconj(w));
 }
 
 // ---------------------------------------------------------------- butterflies
@@ -60,16 +90,16 @@ template <int DIR, int S, typename C> __device__ __forceinline__ void bfly4(C* v
 
 template <int DIR, int S, typename C> __device__ __forceinline__ void bfly8(C* v) {
   using T = decltype(v[0].x);
-  const T h = (T)0.70710678118654752440;  // 1/sqrt(2)
+  constexpr KC<T> h(0.70710678118654752440);  // 1/sqrt(2)
   C e[4] = {v[0], v[2 * S], v[4 * S], v[6 * S]};
   C o[4] = {v[S], v[3 * S], v[5 * S], v[7 * S]};
   bfly4<DIR, 1>(e);
   bfly4<DIR, 1>(o);
   // o[k] *= exp(DIR * 2 pi i k / 8)
   C o1 = o[1], o3 = o[3];
-  o[1] = C{h * (o1.x - DIR * o1.y), h * (o1.y + DIR * o1.x)};
+  o[1] = C{h.mul(o1.x - DIR * o1.y), h.mul(o1.y + DIR * o1.x)};
   o[2] = rot<DIR>(o[2]);
-  o[3] = C{h * (-o3.x - DIR * o3.y), h * (-o3.y + DIR * o3.x)};
+  o[3] = C{h.mul(-o3.x - DIR * o3.y), h.mul(-o3.y + DIR * o3.x)};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     v[k * S] = cadd(e[k], o[k]);
@@ -79,11 +109,12 @@ template <int DIR, int S, typename C> __device__ __forceinline__ void bfly8(C* v
 
 template <int DIR, int S, typename C> __device__ __forceinline__ void bfly3(C* v) {
   using T = decltype(v[0].x);
-  const T c1 = (T)-0.5, s1 = (T)0.86602540378443864676;  // cos, sin of 2 pi/3
+  const T c1 = (T)-0.5;                        // cos 2 pi/3 (exact)
+  constexpr KC<T> s1(0.86602540378443864676);  // sin 2 pi/3
   C a = v[0], b = v[S], c = v[2 * S];
   C s = cadd(b, c), d = csub(b, c);
   C t = C{a.x + c1 * s.x, a.y + c1 * s.y};
-  C u = rot<DIR>(cscale(d, s1));
+  C u = rot<DIR>(C{s1.mul(d.x), s1.mul(d.y)});
   v[0] = cadd(a, s);
   v[S] = cadd(t, u);
   v[2 * S] = csub(t, u);
@@ -91,14 +122,14 @@ template <int DIR, int S, typename C> __device__ __forceinline__ void bfly3(C* v
 
 template <int DIR, int S, typename C> __device__ __forceinline__ void bfly5(C* v) {
   using T = decltype(v[0].x);
-  const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;  // cos 2pi/5, cos 4pi/5
-  const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;  // sin 2pi/5, sin 4pi/5
+  constexpr KC<T> c1(0.30901699437494742410), c2(-0.80901699437494742410);  // cos 2pi/5, cos 4pi/5
+  constexpr KC<T> s1(0.95105651629515357212), s2(0.58778525229247312917);   // sin 2pi/5, sin 4pi/5
   C a = v[0], b = v[S], c = v[2 * S], d = v[3 * S], e = v[4 * S];
   C p1 = cadd(b, e), m1 = csub(b, e), p2 = cadd(c, d), m2 = csub(c, d);
-  C t1 = C{a.x + c1 * p1.x + c2 * p2.x, a.y + c1 * p1.y + c2 * p2.y};
-  C t2 = C{a.x + c2 * p1.x + c1 * p2.x, a.y + c2 * p1.y + c1 * p2.y};
-  C u1 = rot<DIR>(C{s1 * m1.x + s2 * m2.x, s1 * m1.y + s2 * m2.y});
-  C u2 = rot<DIR>(C{s2 * m1.x - s1 * m2.x, s2 * m1.y - s1 * m2.y});
+  C t1 = C{a.x + c1.mul(p1.x) + c2.mul(p2.x), a.y + c1.mul(p1.y) + c2.mul(p2.y)};
+  C t2 = C{a.x + c2.mul(p1.x) + c1.mul(p2.x), a.y + c2.mul(p1.y) + c1.mul(p2.y)};
+  C u1 = rot<DIR>(C{s1.mul(m1.x) + s2.mul(m2.x), s1.mul(m1.y) + s2.mul(m2.y)});
+  C u2 = rot<DIR>(C{s2.mul(m1.x) - s1.mul(m2.x), s2.mul(m1.y) - s1.mul(m2.y)});
   v[0] = C{a.x + p1.x + p2.x, a.y + p1.y + p2.y};
   v[S] = cadd(t1, u1);
   v[4 * S] = csub(t1, u1);
@@ -150,10 +181,10 @@ __host__ __device__ constexpr int num_stages(int N, int E) {
 //
 // v      : E registers, v[m] <-> position t + P*m
 // sm     : this line's exchange buffer, position p at sm[p * SS]
-// tw     : twiddle table, tw[j * TWS] = exp(-2 pi i j / N) for j < N
+// tw     : twiddle table, tw[j * TWS] = exp(-2 pi i j / N) for j < N (twv<T>)
 // All threads of the block must call this together (it synchronises).
 template <typename T, int N, int E, int DIR, int NS = 1>
-__device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, const cx<T>* tw, int TWS) {
+__device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, const twv<T>* tw, int TWS) {
   using C = cx<T>;
   if constexpr (NS < N) {
     constexpr int P = N / E;

@@ -27,10 +27,10 @@ template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
 }
 
 template <typename T, int M>
-static cudaError_t x_r2c_n(const T* e, const T* h, cx<T>* out, long rows3, long nrows, const cx<T>* tw, cudaStream_t s) {
+static cudaError_t x_r2c_n(const T* e, const T* h, cx<T>* out, long rows3, long nrows, const twv<T>* tw, cudaStream_t s) {
   constexpr int E = fft_E(M), TY = fft_TY(M), P = M / E;
   static_assert(plan_ok(M, E), "plan");
-  const size_t smem = sizeof(cx<T>) * (2 * M + TY * (M + 1));
+  const size_t smem = sizeof(twv<T>) * 2 * M + sizeof(cx<T>) * TY * (M + 1);
   auto k = k_x_r2c<T, M, E, TY>;
   cudaError_t err = set_smem(k, smem);
   if (err != cudaSuccess) return err;
@@ -40,9 +40,10 @@ static cudaError_t x_r2c_n(const T* e, const T* h, cx<T>* out, long rows3, long 
 }
 
 template <typename T, int M>
-static cudaError_t x_c2r_n(const cx<T>* in, T* e, T* h, long rows3, long nrows, const cx<T>* tw, T scale, cudaStream_t s) {
+static cudaError_t x_c2r_n(const cx<T>* in, T* e, T* h, long rows3, long nrows, const twv<T>* tw, double scale,
+                           cudaStream_t s) {
   constexpr int E = fft_E(M), TY = fft_TY(M), P = M / E;
-  const size_t smem = sizeof(cx<T>) * (2 * M + TY * (M + 1));
+  const size_t smem = sizeof(twv<T>) * 2 * M + sizeof(cx<T>) * TY * (M + 1);
   auto k = k_x_c2r<T, M, E, TY>;
   cudaError_t err = set_smem(k, smem);
   if (err != cudaSuccess) return err;
@@ -52,10 +53,10 @@ static cudaError_t x_c2r_n(const cx<T>* in, T* e, T* h, long rows3, long nrows, 
 }
 
 template <typename T, int N, int DIR>
-static cudaError_t strided_n(cx<T>* data, long inner, long outer, const cx<T>* tw, cudaStream_t s) {
+static cudaError_t strided_n(cx<T>* data, long inner, long outer, const twv<T>* tw, cudaStream_t s) {
   constexpr int E = fft_E(N), TX = fft_TX(N), P = N / E;
   static_assert(plan_ok(N, E), "plan");
-  const size_t smem = sizeof(cx<T>) * (N + N * TX);
+  const size_t smem = sizeof(twv<T>) * N + sizeof(cx<T>) * N * TX;
   auto k = k_fft_strided<T, N, E, TX, DIR>;
   cudaError_t err = set_smem(k, smem);
   if (err != cudaSuccess) return err;
@@ -66,7 +67,7 @@ static cudaError_t strided_n(cx<T>* data, long inner, long outer, const cx<T>* t
 }
 
 template <typename T>
-cudaError_t launch_x_r2c(int M, const T* e, const T* h, cx<T>* out, long rows3, long nrows, const cx<T>* tw, cudaStream_t s) {
+cudaError_t launch_x_r2c(int M, const T* e, const T* h, cx<T>* out, long rows3, long nrows, const twv<T>* tw, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   switch (M) {
 #define X(n) case n: return x_r2c_n<T, n>(e, h, out, rows3, nrows, tw, s);
@@ -77,7 +78,8 @@ cudaError_t launch_x_r2c(int M, const T* e, const T* h, cx<T>* out, long rows3, 
 }
 
 template <typename T>
-cudaError_t launch_x_c2r(int M, const cx<T>* in, T* e, T* h, long rows3, long nrows, const cx<T>* tw, T scale, cudaStream_t s) {
+cudaError_t launch_x_c2r(int M, const cx<T>* in, T* e, T* h, long rows3, long nrows, const twv<T>* tw, double scale,
+                         cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   switch (M) {
 #define X(n) case n: return x_c2r_n<T, n>(in, e, h, rows3, nrows, tw, scale, s);
@@ -88,7 +90,7 @@ cudaError_t launch_x_c2r(int M, const cx<T>* in, T* e, T* h, long rows3, long nr
 }
 
 template <typename T>
-cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const cx<T>* tw, cudaStream_t s) {
+cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const twv<T>* tw, cudaStream_t s) {
   if (inner <= 0 || outer <= 0 || N == 1) return cudaSuccess;
   if (dir < 0) {
     switch (N) {

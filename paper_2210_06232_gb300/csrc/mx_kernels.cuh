@@ -168,33 +168,28 @@ __global__ void k_coef_table(CoefT* __restrict__ tab, int nq, GridParams g, doub
 //       w = k x E, v = k x H                     -> H2 = s9/N_S^2
 //   s10+w k_w Im(conj(H).E)                      -> M1[w] = -s/N_S^2, M2 = -M1
 //   s13 eps^2 |k.E|^2,  s14 mu^2 |k.H|^2         -> ||div||_N = sqrt(s)/N_S
+// Two identities for real k shorten the arithmetic:
+//   |k x U|^2 = |k|^2 |U|^2 - |k.U|^2            (Lagrange)
+//   k.((k x a) x (k x b)) = |k|^2 k.(a x b)       ((k x a) x (k x b) = (k.(a x b)) k)
 // Each density is multiplied by the Hermitian weight of its half-spectrum
 // column (1 for the packed column 0, 2 otherwise).
 template <typename T>
 __device__ __forceinline__ void add_densities(T* acc, T w, T kx, T ky, T kz, const cx<T>* h, const cx<T>* e, T eps, T mu) {
-  using C = cx<T>;
   const T h2 = h[0].x * h[0].x + h[0].y * h[0].y + h[1].x * h[1].x + h[1].y * h[1].y + h[2].x * h[2].x + h[2].y * h[2].y;
   const T e2 = e[0].x * e[0].x + e[0].y * e[0].y + e[1].x * e[1].x + e[1].y * e[1].y + e[2].x * e[2].x + e[2].y * e[2].y;
-  C we[3] = {C{ky * e[2].x - kz * e[1].x, ky * e[2].y - kz * e[1].y},
-             C{kz * e[0].x - kx * e[2].x, kz * e[0].y - kx * e[2].y},
-             C{kx * e[1].x - ky * e[0].x, kx * e[1].y - ky * e[0].y}};
-  C vh[3] = {C{ky * h[2].x - kz * h[1].x, ky * h[2].y - kz * h[1].y},
-             C{kz * h[0].x - kx * h[2].x, kz * h[0].y - kx * h[2].y},
-             C{kx * h[1].x - ky * h[0].x, kx * h[1].y - ky * h[0].y}};
-  const T w2 = we[0].x * we[0].x + we[0].y * we[0].y + we[1].x * we[1].x + we[1].y * we[1].y + we[2].x * we[2].x + we[2].y * we[2].y;
-  const T v2 = vh[0].x * vh[0].x + vh[0].y * vh[0].y + vh[1].x * vh[1].x + vh[1].y * vh[1].y + vh[2].x * vh[2].x + vh[2].y * vh[2].y;
+  const T kEr = kx * e[0].x + ky * e[1].x + kz * e[2].x, kEi = kx * e[0].y + ky * e[1].y + kz * e[2].y;
+  const T kHr = kx * h[0].x + ky * h[1].x + kz * h[2].x, kHi = kx * h[0].y + ky * h[1].y + kz * h[2].y;
+  const T kE2 = kEr * kEr + kEi * kEi, kH2 = kHr * kHr + kHi * kHi;
+  const T k2 = kx * kx + ky * ky + kz * kz;
+  // k . (Re U x Im U)
+  const T ch = kx * (h[1].x * h[2].y - h[2].x * h[1].y) + ky * (h[2].x * h[0].y - h[0].x * h[2].y) +
+               kz * (h[0].x * h[1].y - h[1].x * h[0].y);
+  const T ce = kx * (e[1].x * e[2].y - e[2].x * e[1].y) + ky * (e[2].x * e[0].y - e[0].x * e[2].y) +
+               kz * (e[0].x * e[1].y - e[1].x * e[0].y);
+  const T ie = (T)1 / eps, im = (T)1 / mu;
   const T d0 = w * (mu * h2 + eps * e2);
-  const T d1 = w * (w2 / mu + v2 / eps);
-  // k . (a x b) for a = Re, b = Im
-  auto kcross = [&](const C* a) -> T {
-    return kx * (a[1].x * a[2].y - a[2].x * a[1].y) + ky * (a[2].x * a[0].y - a[0].x * a[2].y) +
-           kz * (a[0].x * a[1].y - a[1].x * a[0].y);
-  };
-  const T hel1 = w * (kcross(h) / eps + kcross(e) / mu);
-  const T hel2 = w * (kcross(we) / (eps * mu * mu) + kcross(vh) / (mu * eps * eps));
+  const T d1 = w * ((k2 * e2 - kE2) * im + (k2 * h2 - kH2) * ie);
   const T mim = w * (h[0].x * e[0].y - h[0].y * e[0].x + h[1].x * e[1].y - h[1].y * e[1].x + h[2].x * e[2].y - h[2].y * e[2].x);
-  const C kE = C{kx * e[0].x + ky * e[1].x + kz * e[2].x, kx * e[0].y + ky * e[1].y + kz * e[2].y};
-  const C kH = C{kx * h[0].x + ky * h[1].x + kz * h[2].x, kx * h[0].y + ky * h[1].y + kz * h[2].y};
   acc[0] += d0;
   acc[1] += d1;
   acc[2] += kx * kx * d0;
@@ -203,13 +198,13 @@ __device__ __forceinline__ void add_densities(T* acc, T w, T kx, T ky, T kz, con
   acc[5] += kx * kx * d1;
   acc[6] += ky * ky * d1;
   acc[7] += kz * kz * d1;
-  acc[8] += hel1;
-  acc[9] += hel2;
+  acc[8] += w * (ch * ie + ce * im);
+  acc[9] += w * k2 * (ce * ie * im * im + ch * im * ie * ie);
   acc[10] += kx * mim;
   acc[11] += ky * mim;
   acc[12] += kz * mim;
-  acc[13] += w * eps * eps * (kE.x * kE.x + kE.y * kE.y);
-  acc[14] += w * mu * mu * (kH.x * kH.x + kH.y * kH.y);
+  acc[13] += w * eps * eps * kE2;
+  acc[14] += w * mu * mu * kH2;
 }
 
 // Block-wide FP64 reduction of NSUM values, then a deterministic grid
@@ -277,13 +272,13 @@ __device__ __forceinline__ void reduce_and_finish(double* acc, double* __restric
 template <typename T, int M, int E, int TY>
 __global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in_e, const T* __restrict__ in_h,
                                                         cx<T>* __restrict__ out, long rows3, long nrows,
-                                                        const cx<T>* __restrict__ twg) {
+                                                        const twv<T>* __restrict__ twg) {
   using C = cx<T>;
   constexpr int P = M / E;
   constexpr int PITCH = M + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C* tw = reinterpret_cast<C*>(smraw);  // 2M entries: exp(-2 pi i j / (2M))
-  C* sm = tw + 2 * M;
+  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);  // 2M entries: exp(-2 pi i j / (2M))
+  C* sm = reinterpret_cast<C*>(tw + 2 * M);
   for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) tw[i] = twg[i];
   const int t = threadIdx.x % P, ly = threadIdx.x / P;
   const long row = (long)blockIdx.x * TY + ly;
@@ -315,7 +310,7 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in
       C zp = cconj(line[M - k]);
       C a = cadd(z, zp), d = csub(z, zp);   // 2A, 2iB
       C b = C{d.y, -d.x};                    // 2B = -i * d
-      C wb = cmul(tw[k], b);
+      C wb = twmul<-1>(b, tw[k]);
       r = C{(T)0.5 * (a.x + wb.x), (T)0.5 * (a.y + wb.y)};
     }
     dst[k] = r;
@@ -328,13 +323,13 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in
 template <typename T, int M, int E, int TY>
 __global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict__ in, T* __restrict__ out_e,
                                                         T* __restrict__ out_h, long rows3, long nrows,
-                                                        const cx<T>* __restrict__ twg, T scale) {
+                                                        const twv<T>* __restrict__ twg, double scale) {
   using C = cx<T>;
   constexpr int P = M / E;
   constexpr int PITCH = M + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C* tw = reinterpret_cast<C*>(smraw);
-  C* sm = tw + 2 * M;
+  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);
+  C* sm = reinterpret_cast<C*>(tw + 2 * M);
   for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) tw[i] = twg[i];
   const int t = threadIdx.x % P, ly = threadIdx.x / P;
   const long row = (long)blockIdx.x * TY + ly;
@@ -357,17 +352,18 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict_
     } else {
       C xp = cconj(line[M - k]);
       C s = cadd(x, xp), d = csub(x, xp);
-      C wd = cmul(cconj(tw[k]), d);
+      C wd = twmul<+1>(d, tw[k]);
       v[m] = C{s.x - wd.y, s.y + wd.x};  // s + i * wd
     }
   }
   line_fft<T, M, E, +1>(v, line, 1, t, tw, 2);
   if (!ok) return;
   T* dst = row < rows3 ? out_e + row * (2L * M) : out_h + (row - rows3) * (2L * M);
+  const KC<T> sc(scale);  // 1/(Nx Ny Nz), hi + lo in FP32
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int n = t + P * m;
-    *reinterpret_cast<C*>(dst + 2 * n) = C{v[m].x * scale, v[m].y * scale};
+    *reinterpret_cast<C*>(dst + 2 * n) = C{sc.mul(v[m].x), sc.mul(v[m].y)};
   }
 }
 
@@ -378,12 +374,12 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict_
 // Block = TX consecutive inner indices x P threads per line.
 template <typename T, int N, int E, int TX, int DIR>
 __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict__ data, long inner,
-                                                              const cx<T>* __restrict__ twg) {
+                                                              const twv<T>* __restrict__ twg) {
   using C = cx<T>;
   constexpr int P = N / E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C* tw = reinterpret_cast<C*>(smraw);
-  C* sm = tw + N;
+  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);
+  C* sm = reinterpret_cast<C*>(tw + N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
   const int x = threadIdx.x % TX, t = threadIdx.x / TX;
   const long col = (long)blockIdx.x * TX + x;

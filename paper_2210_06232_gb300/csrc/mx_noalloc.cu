@@ -86,16 +86,20 @@ extern "C" mx_status mx_spectral_update_noalloc(const void* spec_in, void* spec_
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* scratch = nullptr;
   if (scratch_ptr(&scratch) != cudaSuccess) return MX_E_CUDA;
-  // the block counter must start at zero (the last block also resets it)
-  if (cudaMemsetAsync(scratch + COUNTER_OFF, 0, sizeof(unsigned), s) != cudaSuccess) return MX_E_CUDA;
+  // the block counter and the wait-timeout flag after it must start at zero
+  if (cudaMemsetAsync(scratch + COUNTER_OFF, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return MX_E_CUDA;
   cudaError_t e = precision == MX_FP64 ? launch<double>(mode, spec_in, spec_out, npts, g, t, blocks, scratch, s)
                                        : launch<float>(mode, spec_in, spec_out, npts, g, t, blocks, scratch, s);
   if (e != cudaSuccess) return MX_E_CUDA;
   if (!inv_out) return MX_OK;
   double sums[16];
+  unsigned flags[2];
   if (cudaMemcpyAsync(sums, scratch + RECORD_OFF, sizeof(sums), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return MX_E_CUDA;
+  if (cudaMemcpyAsync(flags, scratch + COUNTER_OFF, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return MX_E_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MX_E_CUDA;
+  if (flags[1]) return MX_E_TIMEOUT;
   const double N = (double)nx * ny * nz, N2 = N * N;
   mx_invariants& r = *inv_out;
   memset(&r, 0, sizeof(r));

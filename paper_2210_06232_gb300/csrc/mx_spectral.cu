@@ -1,6 +1,7 @@
 // Spectral pass (per-k exponential update and invariant sums) and the
 // coefficient-table kernel, instantiated for float and double.
 #include "mx_launch.h"
+#include "mx_spectral_tma.cuh"
 
 namespace mx {
 
@@ -41,10 +42,33 @@ static cudaError_t spectral_mode(int mode, const cx<T>* src, cx<T>* dst, long np
   return spectral_v<T, CoefT, TABLE, 1>(mode, src, dst, npts, g, tab, t, blocks, partials, counter, record, s);
 }
 
+template <bool UPDATE, bool INV>
+static cudaError_t tma_mode(const float2* src, float2* dst, long npts, const GridParams& g, const void* tab, int blocks,
+                            double* partials, unsigned* counter, double* record, cudaStream_t s) {
+  auto k = k_spectral_tma<UPDATE, INV>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k<<<blocks, TMA_THREADS, tma_smem_bytes(), s>>>(src, dst, npts, g, (const Coef<float>*)tab, partials, counter, record);
+  return cudaGetLastError();
+}
+
 template <>
 cudaError_t launch_spectral<float>(int mode, int coef_kind, const float2* src, float2* dst, long npts, const GridParams& g,
                                    const void* tab, double t, int blocks, double* partials, unsigned* counter,
                                    double* record, cudaStream_t s) {
+  // bulk-copy pipeline: table coefficients, even rows, 16-byte aligned buffers
+  const bool aligned = (((uintptr_t)src | (uintptr_t)dst) & 15u) == 0;
+  if (coef_kind == 0 && g.mx % 2 == 0 && aligned && npts < (1L << 31) && npts >= TMA_CH) {
+    switch (mode) {
+      case 0: return tma_mode<false, true>(src, dst, npts, g, tab, blocks, partials, counter, record, s);
+      case 1: return tma_mode<true, false>(src, dst, npts, g, tab, blocks, partials, counter, record, s);
+      case 2: return tma_mode<true, true>(src, dst, npts, g, tab, blocks, partials, counter, record, s);
+    }
+  }
   switch (coef_kind) {
     case 0: return spectral_mode<float, Coef<float>, true>(mode, src, dst, npts, g, tab, t, blocks, partials, counter, record, s);
     case 1: return spectral_mode<float, CoefHL, true>(mode, src, dst, npts, g, tab, t, blocks, partials, counter, record, s);

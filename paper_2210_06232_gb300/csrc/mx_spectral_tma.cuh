@@ -1,0 +1,225 @@
+// FP32 spectral pass with a bulk-copy (TMA engine) pipeline, sm_103a.
+//
+// The pass is a pure stream: per point it reads six complex values, applies
+// the per-k exponential and writes six.  Memory-level parallelism comes from
+// the copy engine instead of registers: chunks of CH points per component
+// are brought into shared memory by cp.async.bulk (one 4 KB copy per
+// component) completing on an mbarrier, NST chunks in flight per block;
+// 256 threads consume a chunk (two points each) and write the result with
+// streaming 16-byte stores.  Waits on the mbarrier are bounded: a wait that
+// gives up sets counter[1] (read by the host as MX_E_TIMEOUT) and the block
+// leaves the loop at the next block-wide vote.
+#pragma once
+#include "mx_kernels.cuh"
+
+namespace mx {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false when the limit was reached
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < (1u << 24); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Orders this thread's generic-proxy shared-memory reads before later
+// async-proxy (bulk copy) writes to the same bytes: without it a refill of a
+// released stage can overtake the reads of that stage.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int TMA_CH = 512;       // points per component per chunk (4 KB in FP32)
+constexpr int TMA_NST = 4;        // chunks in flight per block
+constexpr int TMA_CONSUMERS = 256;
+constexpr int TMA_THREADS = TMA_CONSUMERS + 32;  // + one producer warp
+constexpr int TMA_CWARPS = TMA_CONSUMERS / 32;
+constexpr size_t tma_smem_bytes() {
+  return (size_t)TMA_NST * 6 * TMA_CH * sizeof(float2) + 16 * TMA_NST + (size_t)TMA_CWARPS * NSUM * sizeof(double);
+}
+
+// Warp-specialised: warp TMA_CWARPS is the producer (lane 0 issues the bulk
+// copies of chunk i into stage i % NST once `empty` says the consumers have
+// read what was there); the consumer warps wait on `full`, copy their two
+// points per component to registers, fence their generic reads against the
+// async proxy, release the stage, then compute and store.  Coefficient-table loads are issued before the wait on the data.
+template <bool UPDATE, bool INV>
+__global__ void __launch_bounds__(TMA_THREADS, 2)
+    k_spectral_tma(const float2* __restrict__ src, float2* __restrict__ dst, long comp_stride, GridParams g,
+                   const Coef<float>* __restrict__ tab, double* __restrict__ partials, unsigned* __restrict__ counter,
+                   double* __restrict__ record) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* stage = reinterpret_cast<float2*>(smraw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smraw + (size_t)TMA_NST * 6 * TMA_CH * sizeof(float2));
+  uint64_t* empty = full + TMA_NST;
+  double* wsum = reinterpret_cast<double*>(empty + TMA_NST);  // [TMA_CWARPS][NSUM]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned npts = (unsigned)comp_stride;
+  const unsigned nchunks = (npts + TMA_CH - 1) / TMA_CH;
+
+  if (tid == 0) {
+    for (int s = 0; s < TMA_NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], TMA_CONSUMERS);
+    }
+    mbar_fence_init();
+  }
+  if (tid < TMA_CWARPS * NSUM) wsum[tid] = 0.0;
+  __syncthreads();
+
+  if (warp == TMA_CWARPS) {
+    // ---------------------------------------------------------- producer
+    if (lane == 0) {
+      unsigned i = 0;
+      bool ok = true;
+      for (unsigned c = blockIdx.x; c < nchunks; c += gridDim.x, ++i) {
+        const int s = (int)(i % TMA_NST);
+        if (i >= (unsigned)TMA_NST && !mbar_wait_bounded(&empty[s], ((i / TMA_NST) - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        const unsigned p0 = c * TMA_CH;
+        const unsigned n = min((unsigned)TMA_CH, npts - p0);
+        const uint32_t bytes = n * (uint32_t)sizeof(float2);
+        mbar_expect_tx(&full[s], 6 * bytes);
+#pragma unroll
+        for (int comp = 0; comp < 6; ++comp)
+          bulk_g2s(stage + ((size_t)s * 6 + comp) * TMA_CH, src + (size_t)comp * comp_stride + p0, bytes, &full[s]);
+      }
+      if (!ok) {
+        atomicExch(counter + 1, 1u);
+        // let the last copies this block issued land before its shared memory is released
+        for (unsigned j = (i > (unsigned)TMA_NST ? i - TMA_NST : 0); j < i; ++j)
+          mbar_wait_bounded(&full[j % TMA_NST], (j / TMA_NST) & 1u);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------- consumers
+    const unsigned mx = (unsigned)g.mx, ny = (unsigned)g.ny;
+    const float eps = (float)g.eps, mu = (float)g.mu;
+    const float nux = (float)g.nu[0], nuy = (float)g.nu[1], nuz = (float)g.nu[2];
+    float part[INV ? NSUM : 1];
+#pragma unroll
+    for (int k = 0; k < (INV ? NSUM : 1); ++k) part[k] = 0.f;
+    int cnt = 0;
+    unsigned i = 0;
+    for (unsigned c = blockIdx.x; c < nchunks; c += gridDim.x, ++i) {
+      const int s = (int)(i % TMA_NST);
+      const unsigned p = c * TMA_CH + 2 * tid;
+      const bool live = p < npts;
+      const unsigned pp = live ? p : 0;
+      const unsigned r = pp / mx;
+      const int x0 = (int)(pp - r * mx);
+      const unsigned z = r / ny;
+      const int y = (int)(r - z * ny);
+      const int my = signed_index(y, g.ny), mz = signed_index((int)z, g.nz);
+      float4 q4[2];
+      if constexpr (UPDATE) {
+        const int qyz = g.qa[1] * my * my + g.qa[2] * mz * mz;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+          q4[j] = __ldg(reinterpret_cast<const float4*>(tab) + (g.qa[0] * (x0 + j) * (x0 + j) + qyz));
+      }
+      if (!mbar_wait_bounded(&full[s], (i / TMA_NST) & 1u)) {
+        atomicExch(counter + 1, 1u);
+        break;
+      }
+      const float4* st4 = reinterpret_cast<const float4*>(stage + (size_t)s * 6 * TMA_CH) + tid;
+      float4 v[6];
+#pragma unroll
+      for (int comp = 0; comp < 6; ++comp) v[comp] = st4[comp * (TMA_CH / 2)];
+      fence_proxy_async_smem();
+      mbar_arrive(&empty[s]);
+      if (!live) continue;
+      const float ky = nuy * (float)my, kz = nuz * (float)mz;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int x = x0 + j;
+        const float kx = nux * (float)x;
+        float2 ee[3], hh[3];
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp) {
+          ee[comp] = j ? make_float2(v[comp].z, v[comp].w) : make_float2(v[comp].x, v[comp].y);
+          hh[comp] = j ? make_float2(v[comp + 3].z, v[comp + 3].w) : make_float2(v[comp + 3].x, v[comp + 3].y);
+        }
+        if constexpr (UPDATE) {
+          const Coef<float> q{q4[j].x, q4[j].y, q4[j].z, q4[j].w};
+          Apply<float, Coef<float>>::run(q, kx, ky, kz, hh, ee);
+#pragma unroll
+          for (int comp = 0; comp < 3; ++comp) {
+            if (j) {
+              v[comp].z = ee[comp].x, v[comp].w = ee[comp].y;
+              v[comp + 3].z = hh[comp].x, v[comp + 3].w = hh[comp].y;
+            } else {
+              v[comp].x = ee[comp].x, v[comp].y = ee[comp].y;
+              v[comp + 3].x = hh[comp].x, v[comp + 3].y = hh[comp].y;
+            }
+          }
+        }
+        if constexpr (INV) add_densities<float>(part, x == 0 ? 1.f : 2.f, kx, ky, kz, hh, ee, eps, mu);
+      }
+      if constexpr (UPDATE) {
+#pragma unroll
+        for (int comp = 0; comp < 6; ++comp)
+          __stcs(reinterpret_cast<float4*>(dst + (size_t)comp * comp_stride + p), v[comp]);
+      }
+      if constexpr (INV) {
+        if (++cnt == 16) {  // 32 points per thread in FP32, then FP64 per warp
+#pragma unroll
+          for (int k = 0; k < NSUM; ++k) {
+            float w = part[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            if (lane == 0) wsum[warp * NSUM + k] += (double)w;
+            part[k] = 0.f;
+          }
+          cnt = 0;
+        }
+      }
+    }
+    if constexpr (INV) {
+#pragma unroll
+      for (int k = 0; k < NSUM; ++k) {
+        float w = part[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0) wsum[warp * NSUM + k] += (double)w;
+      }
+    }
+  }
+  if constexpr (INV) {
+    __syncthreads();
+    double acc[NSUM];
+#pragma unroll
+    for (int k = 0; k < NSUM; ++k) acc[k] = (lane == 0 && warp < TMA_CWARPS) ? wsum[warp * NSUM + k] : 0.0;
+    reduce_and_finish(acc, partials, counter, record);
+  }
+}
+
+}  // namespace mx

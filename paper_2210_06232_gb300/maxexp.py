@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "lib", "libmaxexp.so")
+LIB_PATH = os.environ.get("MAXEXP_LIB") or os.path.join(_PKG, "lib", "libmaxexp.so")
 
 MX_OK, MX_E_INVAL, MX_E_UNSUPPORTED_N, MX_E_NOMEM, MX_E_CUDA, MX_E_TIMEOUT, MX_E_STATE = range(7)
 MX_FP64, MX_FP32 = 0, 1

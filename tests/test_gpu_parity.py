@@ -162,6 +162,32 @@ def test_reversibility_and_zero_step():
         s.close()
 
 
+@pytest.mark.parametrize("n", [128, 160])
+def test_fp32_spectral_multichunk_blocks(n):
+    """Grids where each block of the pipelined FP32 pass streams many chunks (stage buffers
+    reused): FP32 and FP64 spectral forms agree to FP32 round-off."""
+    import torch
+
+    mx = _mx()
+    res = {}
+    for P in (mx.MX_FP64, mx.MX_FP32):
+        s = mx.Solver((n, n, n), (0, 0, 0), (TWO_PI,) * 3, 1.3, 0.8, P, mx.MX_FORM_SPECTRAL)
+        s.load_random(5, n / 16)
+        s.step(0.02, 9, 1)
+        dt = torch.float64 if P == mx.MX_FP64 else torch.float32
+        E = torch.empty((3, n, n, n), dtype=dt, device="cuda")
+        Hh = torch.empty_like(E)
+        s.read(E, Hh)
+        s.sync()
+        res[P] = (E.double().cpu().numpy(), Hh.double().cpu().numpy(), s.invariants())
+        s.close()
+    E64, H64, i64 = res[mx.MX_FP64]
+    E32, H32, i32 = res[mx.MX_FP32]
+    assert rel_l2(E32, H32, E64, H64) < 1e-6
+    sc = inv_scales(i64[0], 1.3, 0.8)
+    assert max(inv_diff(a, b, sc) for a, b in zip(i32, i64)) < 1e-6
+
+
 def test_deterministic_invariants():
     """Same input, same launch: bitwise identical invariant records and fields."""
     mx = _mx()
