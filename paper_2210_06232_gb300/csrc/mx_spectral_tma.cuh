@@ -129,23 +129,40 @@ __global__ void __launch_bounds__(TMA_THREADS, 2)
     for (int k = 0; k < (INV ? NSUM : 1); ++k) part[k] = 0.f;
     int cnt = 0;
     unsigned i = 0;
-    for (unsigned c = blockIdx.x; c < nchunks; c += gridDim.x, ++i) {
-      const int s = (int)(i % TMA_NST);
+    // position of this thread's two points in chunk c, and their table entries
+    struct Pos {
+      unsigned p;
+      int x0, my, mz;
+      float4 q[2];
+    };
+    auto locate = [&](unsigned c, Pos& o) {
       const unsigned p = c * TMA_CH + 2 * tid;
-      const bool live = p < npts;
-      const unsigned pp = live ? p : 0;
+      const unsigned pp = p < npts ? p : 0;
       const unsigned r = pp / mx;
-      const int x0 = (int)(pp - r * mx);
+      o.p = p;
+      o.x0 = (int)(pp - r * mx);
       const unsigned z = r / ny;
       const int y = (int)(r - z * ny);
-      const int my = signed_index(y, g.ny), mz = signed_index((int)z, g.nz);
-      float4 q4[2];
+      o.my = signed_index(y, g.ny);
+      o.mz = signed_index((int)z, g.nz);
       if constexpr (UPDATE) {
-        const int qyz = g.qa[1] * my * my + g.qa[2] * mz * mz;
+        const int qyz = g.qa[1] * o.my * o.my + g.qa[2] * o.mz * o.mz;
 #pragma unroll
         for (int j = 0; j < 2; ++j)
-          q4[j] = __ldg(reinterpret_cast<const float4*>(tab) + (g.qa[0] * (x0 + j) * (x0 + j) + qyz));
+          o.q[j] = __ldg(reinterpret_cast<const float4*>(tab) + (g.qa[0] * (o.x0 + j) * (o.x0 + j) + qyz));
       }
+    };
+    Pos cur, nxt;
+    if (blockIdx.x < nchunks) locate(blockIdx.x, cur);
+    // (cur takes nxt at the end of an iteration, when its loads have had the compute time to land)
+    for (unsigned c = blockIdx.x; c < nchunks; c += gridDim.x, ++i, cur = nxt) {
+      const int s = (int)(i % TMA_NST);
+      // table entries of the next chunk are requested before this chunk is computed
+      if (c + gridDim.x < nchunks) locate(c + gridDim.x, nxt);
+      const unsigned p = cur.p;
+      const bool live = p < npts;
+      const int x0 = cur.x0, my = cur.my, mz = cur.mz;
+      const float4 q4[2] = {cur.q[0], cur.q[1]};
       if (!mbar_wait_bounded(&full[s], (i / TMA_NST) & 1u)) {
         atomicExch(counter + 1, 1u);
         break;
