@@ -228,6 +228,54 @@ def form_entry(name, grid, precision, form, ms, steps, prof, peak, inv, world):
     return name, e
 
 
+BATCH_SHAPES = [(32, 32, 32), (48, 64, 80), (64, 64, 64), (96, 96, 64), (128, 128, 128)]
+
+
+def batch_run(torch, mx, peak, steps, warmup, stream, ninst=64, seed=4):
+    """Batched form: 64 FP32 instances of uneven grids, eps, mu in [1, 4], h in [0.01, 0.1], sigma = 8;
+    every step of every instance in one persistent cooperative launch per mx_batch_step call."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for _ in range(ninst):
+        n = BATCH_SHAPES[rng.integers(len(BATCH_SHAPES))]
+        specs.append(dict(n=n, eps=float(rng.uniform(1, 4)), mu=float(rng.uniform(1, 4)), h=float(rng.uniform(0.01, 0.1))))
+    b = mx.Batch(specs, mx.MX_FP32, stream=stream)
+    b.load_random(seed, 8.0)
+    b.step(steps, 1)  # warm-up call: captures the graph for this step count
+    b.sync()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(steps, 1)
+    e1.record(stream)
+    e1.synchronize()
+    b.sync()
+    ms = e0.elapsed_time(e1)
+    pts = sum(int(np.prod(sp["n"])) for sp in specs)
+    drift = 0.0
+    for i in range(ninst):
+        inv = b.instance(i).invariants()
+        e = [r["E1"] for r in inv]
+        drift = max(drift, (max(e) - min(e)) / e[0])
+    used = b.graph_used()
+    b.close()
+    min_bytes = 12 * pts * 4
+    return {
+        "value": pts * steps / (ms / 1e3),
+        "unit": UNIT,
+        "ms_per_step": ms / steps,
+        "instances": ninst,
+        "field_points": pts,
+        "shapes": {"x".join(map(str, sh)): sum(1 for sp in specs if tuple(sp["n"]) == sh) for sh in BATCH_SHAPES},
+        "launches_per_call": 1,
+        "graph_replayed": used,
+        "step_hbm_roofline_frac": (min_bytes / (ms / steps / 1e3) / 1e9) / peak,
+        "energy_rel_drift_max": drift,
+        "dtype": "f32",
+    }
+
+
 def cpu_baseline_sample(budget_s=15.0):
     """The FP64 oracle (numpy, as it stands) on the host cores: Alg. 1 + Alg. 2 at 128^3."""
     import synth
@@ -381,6 +429,7 @@ def main():
             forms[nm] = form_entry(nm, grid, p, f, ms2, k, prof2, peak, inv2, world)[1]
 
     e2e = e2e_run(torch, mx, grid, args.steps, stream)
+    batched = None if args.no_secondary else batch_run(torch, mx, peak, min(args.steps, 100), args.warmup, stream)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline_sample()
@@ -426,6 +475,7 @@ def main():
         "gpu_launches": launches,
         "clocks": ck,
         "forms": forms,
+        "batched": batched,
     }
     print(json.dumps(out), flush=True)
     if dist is not None:

@@ -150,6 +150,61 @@ mx_status mx_read_invariants(mx_ctx* ctx, mx_invariants* out, long long max, lon
  */
 mx_status mx_load_random_divfree(mx_ctx* ctx, unsigned long long seed, double sigma);
 
+/*
+ * FFT schedule autotuner (no counterpart in the paper: it picks launch
+ * shapes).  Each of the six transform passes of this grid shape (x R2C, y
+ * forward, z forward, z inverse, y inverse, x C2R) is timed with every
+ * candidate persistent grid (0, 1, 2, 4, 8 blocks per SM; 0 = one block per
+ * tile) on the context's own work buffers; the fastest is kept in a
+ * process-wide table keyed by (pass, precision, nx, ny, nz) and used by every
+ * context of that shape.  Waits for the stream.  Skipped (MX_OK) while the
+ * stream is being captured, or for a loaded literal-form context (its state
+ * lives in the buffers the timing overwrites); a spectral-form context keeps
+ * its state.  Untuned passes use 4 blocks per SM.
+ */
+mx_status mx_autotune(mx_ctx* ctx);
+/* The schedule in use: bps[0..5] = blocks per SM of the six passes (n >= 6). */
+mx_status mx_schedule(mx_ctx* ctx, int* bps, int n);
+
+/*
+ * Batched form (no counterpart in the paper, which solves one problem at a
+ * time): n independent instances, each its own grid, domain, eps, mu and
+ * step size h, all in the spectral form and one precision, advanced
+ * together.  mx_batch_step(b, K, every) advances every instance K steps of
+ * its own h with ONE persistent cooperative kernel launch (per step: the
+ * coefficient tables of all instances, a grid barrier, the exponential
+ * update of all instances over one chunk list, a grid barrier); the launch
+ * is captured once per K into a CUDA graph and replayed.  Each instance is a
+ * context (mx_batch_instance) for loading, reading fields and invariants and
+ * autotuning.  An instance's fields and invariants are bit-identical whether
+ * it runs alone or in any batch.  Device memory: the instances' contexts
+ * plus about 1 KB of invariant partial sums per 512-point chunk (FP32).
+ */
+typedef struct mx_batch mx_batch;
+typedef struct {
+  int nx, ny, nz;           /* even grid sizes, as for mx_create */
+  double lo[3], hi[3];      /* domain */
+  double eps, mu;           /* positive */
+  double h;                 /* step size of this instance */
+} mx_instance_desc;
+
+mx_status mx_batch_create(mx_batch** out, const mx_instance_desc* inst, int n, int precision, void* stream);
+mx_status mx_batch_size(mx_batch* b, int* n);
+/* Context of instance i (owned by the batch: do not destroy it). */
+mx_status mx_batch_instance(mx_batch* b, int i, mx_ctx** ctx);
+/* mx_load_random_divfree on every instance, instance i with seed + i. */
+mx_status mx_batch_load_random(mx_batch* b, unsigned long long seed, double sigma);
+/* Advance every instance nsteps steps; records invariants as mx_step does. */
+mx_status mx_batch_step(mx_batch* b, long long nsteps, int invariants_every);
+/* Wait for the batch; MX_E_TIMEOUT if a bounded device wait gave up. */
+mx_status mx_batch_sync(mx_batch* b);
+/* 1 when the steps are replayed from a captured CUDA graph, 0 before the
+ * first step, -e when capture was refused with CUDA error e (steps are then
+ * launched directly).  A batch created with a NULL stream uses a stream of
+ * its own (the legacy default stream cannot be captured). */
+mx_status mx_batch_graph_used(mx_batch* b, int* used);
+void mx_batch_destroy(mx_batch* b);
+
 /* Kernel classes timed by mx_profile. */
 typedef enum {
   MX_K_X_R2C = 0,     /* real rows -> packed half spectrum along x */

@@ -1,0 +1,391 @@
+// Batched spectral form: many independent instances (different grids, eps,
+// mu, h) advanced K steps by ONE persistent cooperative launch.
+//
+// Per step n the grid runs
+//   phase A  coefficient tables of every instance at its t_n (grid-stride
+//            over the concatenation of the tables), and the invariant records
+//            of step n-1 (one block per instance, fixed summation order);
+//   barrier
+//   phase B  the exponential update of every instance: a global list of
+//            chunks (CH points x 6 components) spanning all instances, consumed
+//            by the same warp-specialised bulk-copy pipeline as the single
+//            pass; each warp writes its invariant partial sums of the chunk
+//            to `cpart[chunk][warp]` when step n is recorded;
+//   barrier.
+// Chunk contents and warp partitions depend only on the instance's own chunk
+// index, and records are summed per instance over its own chunks in order,
+// so an instance gets bit-identical fields and invariants alone or in any
+// mix.  Grid barriers and mbarrier waits are bounded; a wait that gives up
+// sets bar[2] and every block leaves at its next check.
+#pragma once
+#include "mx_spectral_tma.cuh"
+
+namespace mx {
+
+struct BInst {
+  GridParams g;
+  const void* src;   // spectrum at t0 (packed half spectrum, 6 components)
+  void* dst;         // spectrum at t_n
+  void* tab;         // Coef<T>[nq] for this instance (nullptr: direct coefficients)
+  int nq;
+  unsigned npts;     // Nz * Ny * Mx points per component
+  unsigned chunk0;   // first global chunk of this instance
+  unsigned nchunks;
+  unsigned q0;       // first index of this instance in the concatenated table range
+  unsigned seg0;     // first invariant segment (BT_SEG chunk-warp partials) of this instance
+  unsigned nseg;
+  long long n0;      // step count before this launch
+  double t0, h;      // time before this launch, step size: t_n = t0 + (n - n0) h
+  double* rec;       // record slots of this launch (16 doubles each)
+  int every;         // record every `every` steps (0: none)
+};
+
+struct BatchArgs {
+  const BInst* inst;
+  int ninst;
+  unsigned total_chunks;
+  unsigned total_q;
+  int nsteps;
+  unsigned total_segs;
+  double* cpart;   // [total_chunks][BT_CWARPS][NSUM]: per-warp partial sums of a chunk
+  double* segpart; // [2][total_segs][NSUM]: sums of BT_SEG consecutive chunk-warp partials
+  unsigned* bar;  // [0] arrivals, [1] generation, [2] error flag
+};
+
+template <typename T> struct BTraits;
+template <> struct BTraits<float> {
+  static constexpr int PPT = 2;  // points per consumer thread per chunk
+};
+template <> struct BTraits<double> {
+  static constexpr int PPT = 1;
+};
+constexpr int BT_NST = 4;
+constexpr int BT_CONSUMERS = 256;
+constexpr int BT_THREADS = BT_CONSUMERS + 32;
+constexpr int BT_CWARPS = BT_CONSUMERS / 32;
+constexpr int BT_SEG = 256;  // chunk-warp partials per invariant segment
+template <typename T> __host__ __device__ constexpr int bt_ch() { return BT_CONSUMERS * BTraits<T>::PPT; }
+template <typename T> __host__ __device__ constexpr size_t bt_smem_bytes() {
+  return (size_t)BT_NST * 6 * bt_ch<T>() * sizeof(cx<T>) + 16 * BT_NST + 32 * NSUM * sizeof(double);
+}
+
+// Bounded software grid barrier (all blocks co-resident: cooperative launch).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar) {
+  __syncthreads();
+  __shared__ int failed;
+  if (threadIdx.x == 0) {
+    failed = 0;
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned nb = gridDim.x;
+    if (atomicAdd(bar, 1u) == nb - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned it = 0;
+      while (*gen == g0) {
+        if (++it > (1u << 26) || *(volatile unsigned*)(bar + 2)) {
+          atomicExch(bar + 2, 1u);
+          failed = 1;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return failed == 0 && *(volatile unsigned*)(bar + 2) == 0;
+}
+
+__device__ __forceinline__ int find_inst(const BInst* inst, int n, unsigned key, bool by_chunk) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {  // last instance whose start <= key
+    const int mid = (lo + hi + 1) >> 1;
+    const unsigned start = by_chunk ? __ldg(&inst[mid].chunk0) : __ldg(&inst[mid].q0);
+    if (start <= key) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int find_inst_seg(const BInst* inst, int n, unsigned key) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&inst[mid].seg0) <= key) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ Coef<float> load_coef_cg(const Coef<float>* p) {
+  const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+  return Coef<float>{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Coef<double> load_coef_cg(const Coef<double>* p) {
+  const double2 a = __ldcg(reinterpret_cast<const double2*>(p)), b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+  return Coef<double>{a.x, a.y, b.x, b.y};
+}
+
+__device__ __forceinline__ bool recorded(const BInst& b, long long N) { return b.every > 0 && N % b.every == 0; }
+__device__ __forceinline__ long long rec_slot(const BInst& b, long long N) { return N / b.every - b.n0 / b.every - 1; }
+
+// Transpose reduction of 16 values across a warp (value 15 is padding): after
+// levels with lane offsets 16, 8, 4, 2 each lane keeps one value index,
+// (lane >> 1) & 15, summed over its 16-lane group; the final xor-1 exchange
+// completes the sum over all 32 lanes.  16 shuffles instead of 16 x 5, and
+// the addition order is fixed.
+template <typename T>
+__device__ __forceinline__ T warp_transpose_sum16(T* v, int lane) {
+  // level 16: 8 exchanges
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const bool up = lane & 16;
+    const T send = up ? v[j] : v[j + 8];
+    const T recv = __shfl_xor_sync(0xffffffffu, send, 16);
+    v[j] = (up ? v[j + 8] : v[j]) + recv;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const bool up = lane & 8;
+    const T send = up ? v[j] : v[j + 4];
+    const T recv = __shfl_xor_sync(0xffffffffu, send, 8);
+    v[j] = (up ? v[j + 4] : v[j]) + recv;
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const bool up = lane & 4;
+    const T send = up ? v[j] : v[j + 2];
+    const T recv = __shfl_xor_sync(0xffffffffu, send, 4);
+    v[j] = (up ? v[j + 2] : v[j]) + recv;
+  }
+  {
+    const bool up = lane & 2;
+    const T send = up ? v[0] : v[1];
+    const T recv = __shfl_xor_sync(0xffffffffu, send, 2);
+    v[0] = (up ? v[1] : v[0]) + recv;
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+// Value index held by `lane` after warp_transpose_sum16.
+__device__ __forceinline__ int transpose_index(int lane) {
+  return ((lane & 16) ? 8 : 0) + ((lane & 8) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
+}
+
+// Invariant records, a two-level fixed tree: segment j of an instance is the
+// sum of its chunk-warp partials [j*BT_SEG, (j+1)*BT_SEG) (one warp per
+// segment, lane-strided then a fixed shuffle tree); the record is the sum of
+// the instance's segments (one warp per instance).  Both levels depend only
+// on instance-local indices.
+__device__ __forceinline__ void warp_sum15(double* v) {
+#pragma unroll
+  for (int k = 0; k < NSUM; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
+__device__ void batch_segments(const BatchArgs& a, long long step_local, double* seg) {
+  const int lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned sgi = gw; sgi < a.total_segs; sgi += nw) {
+    const int ii = find_inst_seg(a.inst, a.ninst, sgi);
+    const BInst& b = a.inst[ii];
+    if (!recorded(b, b.n0 + step_local)) continue;  // uniform within the warp
+    const unsigned j = sgi - b.seg0;
+    const unsigned p0 = j * BT_SEG, p1 = min(p0 + BT_SEG, b.nchunks * BT_CWARPS);
+    double v[NSUM];
+#pragma unroll
+    for (int k = 0; k < NSUM; ++k) v[k] = 0.0;
+    for (unsigned pr = p0 + lane; pr < p1; pr += 32) {
+      const double* p = a.cpart + ((size_t)b.chunk0 * BT_CWARPS + pr) * NSUM;
+#pragma unroll
+      for (int k = 0; k < NSUM; ++k) v[k] += __ldcg(p + k);
+    }
+    warp_sum15(v);
+    if (lane < NSUM) {
+      double out = 0.0;
+#pragma unroll
+      for (int k = 0; k < NSUM; ++k) out = (lane == k) ? v[k] : out;
+      seg[(size_t)sgi * NSUM + lane] = out;
+    }
+  }
+}
+
+__device__ void batch_final(const BatchArgs& a, long long step_local, const double* seg) {
+  const int lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned ii = gw; ii < (unsigned)a.ninst; ii += nw) {
+    const BInst& b = a.inst[ii];
+    const long long N = b.n0 + step_local;
+    if (!recorded(b, N)) continue;
+    double v[NSUM];
+#pragma unroll
+    for (int k = 0; k < NSUM; ++k) v[k] = 0.0;
+    for (unsigned j = lane; j < b.nseg; j += 32) {
+      const double* p = seg + (size_t)(b.seg0 + j) * NSUM;
+#pragma unroll
+      for (int k = 0; k < NSUM; ++k) v[k] += __ldcg(p + k);
+    }
+    warp_sum15(v);
+    if (lane < NSUM) {
+      double out = 0.0;
+#pragma unroll
+      for (int k = 0; k < NSUM; ++k) out = (lane == k) ? v[k] : out;
+      b.rec[(size_t)rec_slot(b, N) * 16 + lane] = out;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT_THREADS, 2) k_batch_steps(BatchArgs a) {
+  using C = cx<T>;
+  constexpr int PPT = BTraits<T>::PPT;
+  constexpr int CH = bt_ch<T>();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* stage = reinterpret_cast<C*>(smraw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smraw + (size_t)BT_NST * 6 * CH * sizeof(C));
+  uint64_t* empty = full + BT_NST;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < BT_NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], BT_CONSUMERS);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  unsigned i = 0;  // pipeline position, continues across steps
+  const unsigned gthreads = gridDim.x * blockDim.x;
+
+  for (int n = 1; n <= a.nsteps + 2; ++n) {
+    // ------------------------------------------------ phase A: tables of step n,
+    // invariant segments of step n-1, records of step n-2
+    if (n <= a.nsteps) {
+      for (unsigned q = blockIdx.x * blockDim.x + tid; q < a.total_q; q += gthreads) {
+        const int ii = find_inst(a.inst, a.ninst, q, false);
+        const BInst& b = a.inst[ii];
+        const unsigned qi = q - b.q0;
+        if (b.tab && qi < (unsigned)b.nq)
+          reinterpret_cast<Coef<T>*>(b.tab)[qi] =
+              coef_direct<T, Coef<T>>(b.g.s0 * (double)qi, b.t0 + (double)n * b.h, b.g);
+      }
+    }
+    if (n >= 2 && n - 1 <= a.nsteps) batch_segments(a, n - 1, a.segpart + (size_t)((n - 1) & 1) * a.total_segs * NSUM);
+    if (n >= 3) batch_final(a, n - 2, a.segpart + (size_t)((n - 2) & 1) * a.total_segs * NSUM);
+    if (n == a.nsteps + 2) break;
+    if (!grid_barrier(a.bar)) return;
+    if (n == a.nsteps + 1) continue;
+
+    // ------------------------------------------------ phase B: update every chunk
+    if (warp == BT_CWARPS) {
+      if (lane == 0) {
+        unsigned ii = i;
+        bool ok = true;
+        for (unsigned gc = blockIdx.x; gc < a.total_chunks; gc += gridDim.x, ++ii) {
+          const int s = (int)(ii % BT_NST);
+          if (ii >= (unsigned)BT_NST && !mbar_wait_bounded(&empty[s], ((ii / BT_NST) - 1) & 1u)) {
+            ok = false;
+            break;
+          }
+          const BInst& b = a.inst[find_inst(a.inst, a.ninst, gc, true)];
+          const unsigned p0 = (gc - b.chunk0) * CH;
+          const unsigned cnt = min((unsigned)CH, b.npts - p0);
+          const uint32_t bytes = cnt * (uint32_t)sizeof(C);
+          mbar_expect_tx(&full[s], 6 * bytes);
+          const C* src = reinterpret_cast<const C*>(b.src);
+#pragma unroll
+          for (int comp = 0; comp < 6; ++comp)
+            bulk_g2s(stage + ((size_t)s * 6 + comp) * CH, src + (size_t)comp * b.npts + p0, bytes, &full[s]);
+        }
+        if (!ok) {
+          atomicExch(a.bar + 2, 1u);
+          for (unsigned j = (ii > (unsigned)BT_NST ? ii - BT_NST : 0); j < ii; ++j)
+            mbar_wait_bounded(&full[j % BT_NST], (j / BT_NST) & 1u);
+        }
+      }
+    } else {
+      unsigned ii = i;
+      for (unsigned gc = blockIdx.x; gc < a.total_chunks; gc += gridDim.x, ++ii) {
+        const int s = (int)(ii % BT_NST);
+        const BInst& b = a.inst[find_inst(a.inst, a.ninst, gc, true)];
+        const GridParams& g = b.g;
+        const unsigned p0 = (gc - b.chunk0) * CH;
+        const long long N = b.n0 + n;
+        const bool rec = recorded(b, N);
+        if (!mbar_wait_bounded(&full[s], (ii / BT_NST) & 1u)) {
+          atomicExch(a.bar + 2, 1u);
+          break;
+        }
+        C v[6][PPT];
+        const C* st = stage + (size_t)s * 6 * CH;
+#pragma unroll
+        for (int comp = 0; comp < 6; ++comp)
+#pragma unroll
+          for (int j = 0; j < PPT; ++j) v[comp][j] = st[comp * CH + PPT * tid + j];
+        fence_proxy_async_smem();
+        mbar_arrive(&empty[s]);
+        T part[NSUM];
+#pragma unroll
+        for (int k = 0; k < NSUM; ++k) part[k] = (T)0;
+        const T eps = (T)g.eps, mu = (T)g.mu;
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+          const unsigned p = p0 + PPT * tid + j;
+          if (p >= b.npts) continue;
+          const unsigned r = p / (unsigned)g.mx;
+          const int x = (int)(p - r * (unsigned)g.mx);
+          const unsigned z = r / (unsigned)g.ny;
+          const int y = (int)(r - z * (unsigned)g.ny);
+          const int my = signed_index(y, g.ny), mz = signed_index((int)z, g.nz);
+          const T kx = (T)g.nu[0] * (T)x, ky = (T)g.nu[1] * (T)my, kz = (T)g.nu[2] * (T)mz;
+          Coef<T> q;
+          if (b.tab) {
+            // L1-bypassing load: the table was rewritten by other blocks in phase A
+            q = load_coef_cg(reinterpret_cast<const Coef<T>*>(b.tab) + (g.qa[0] * x * x + g.qa[1] * my * my +
+                                                                        g.qa[2] * mz * mz));
+          } else {
+            const double k2 = g.nu[0] * g.nu[0] * (double)x * x + g.nu[1] * g.nu[1] * (double)my * my +
+                              g.nu[2] * g.nu[2] * (double)mz * mz;
+            q = coef_direct<T, Coef<T>>(k2, b.t0 + (double)n * b.h, g);
+          }
+          C hh[3] = {v[3][j], v[4][j], v[5][j]};
+          C ee[3] = {v[0][j], v[1][j], v[2][j]};
+          Apply<T, Coef<T>>::run(q, kx, ky, kz, hh, ee);
+#pragma unroll
+          for (int comp = 0; comp < 3; ++comp) v[comp][j] = ee[comp], v[comp + 3][j] = hh[comp];
+          if (rec) add_densities<T>(part, x == 0 ? (T)1 : (T)2, kx, ky, kz, hh, ee, eps, mu);
+        }
+        C* dst = reinterpret_cast<C*>(b.dst);
+        const unsigned pt = p0 + PPT * tid;
+        if (pt < b.npts) {
+#pragma unroll
+          for (int comp = 0; comp < 6; ++comp) {
+            if constexpr (PPT == 2) {
+              __stcs(reinterpret_cast<float4*>(dst + (size_t)comp * b.npts + pt),
+                     make_float4(v[comp][0].x, v[comp][0].y, v[comp][PPT - 1].x, v[comp][PPT - 1].y));
+            } else {
+              __stcs(dst + (size_t)comp * b.npts + pt, v[comp][0]);
+            }
+          }
+        }
+        if (rec) {  // uniform across the block: one instance per chunk
+          T v16[16];
+#pragma unroll
+          for (int k = 0; k < NSUM; ++k) v16[k] = part[k];
+          v16[15] = (T)0;
+          const T tot = warp_transpose_sum16<T>(v16, lane);
+          const int idx = transpose_index(lane);
+          if (!(lane & 1) && idx < NSUM) a.cpart[((size_t)gc * BT_CWARPS + warp) * NSUM + idx] = (double)tot;
+        }
+      }
+    }
+    // every thread of a block iterated the same chunks
+    i += (a.total_chunks > blockIdx.x) ? (a.total_chunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    if (!grid_barrier(a.bar)) return;
+  }
+}
+
+}  // namespace mx

@@ -5,6 +5,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/maxexp.h"
@@ -12,44 +14,7 @@
 
 using mx::GridParams;
 
-struct mx_ctx {
-  int nx, ny, nz, mx;
-  double lo[3], hi[3];
-  double eps, mu;
-  int prec, form;
-  cudaStream_t stream;
-  GridParams g;
-  bool table;  // commensurate |k|^2 -> coefficient table
-  int nq;
-  size_t es, cs;  // real / complex element bytes
-  long long ns, nh;
-  void* phys = nullptr;   // 6 * ns reals: literal state; staging for host I/O
-  void* spec = nullptr;   // 6 * nh complex: literal work spectrum; spectral state at t_n
-  void* spec0 = nullptr;  // spectral form: spectrum at load time
-  void* tab = nullptr;
-  void* twx = nullptr;
-  void* twy = nullptr;
-  void* twz = nullptr;
-  double* partials = nullptr;
-  unsigned* counter = nullptr;
-  int sblocks;
-  double* rec = nullptr;
-  long long rec_cap = 0, rec_n = 0;
-  std::vector<double> rec_t;
-  std::vector<long long> rec_step;
-  bool loaded = false;
-  bool spec_valid = false;  // spectral form: `spec` holds the state at `t`
-  double t = 0.0;
-  long long step = 0;
-  int tab_kind = -1;
-  double tab_t = NAN;
-  mx_status err = MX_OK;
-  // per-kernel event timing (mx_profile)
-  bool prof_on = false;
-  std::vector<cudaEvent_t> prof_ev;
-  std::vector<int> prof_kind;
-  size_t prof_used = 0;
-};
+#include "mx_ctx.h"
 
 namespace {
 
@@ -155,7 +120,9 @@ int coef_kind(const mx_ctx* c) {
   return (c->table ? 0 : 2) + (hl ? 1 : 0);
 }
 
-mx_status ensure_records(mx_ctx* c, long long more) {
+}  // namespace
+
+mx_status mx_ensure_records(mx_ctx* c, long long more) {
   if (c->rec_n + more <= c->rec_cap) return MX_OK;
   long long cap = std::max<long long>(c->rec_n + more, std::max<long long>(64, 2 * c->rec_cap));
   double* nr = nullptr;
@@ -170,6 +137,10 @@ mx_status ensure_records(mx_ctx* c, long long more) {
   return MX_OK;
 }
 
+namespace {
+
+mx_status ensure_records(mx_ctx* c, long long more) { return mx_ensure_records(c, more); }
+
 double* next_record(mx_ctx* c, double t, long long step) {
   double* r = c->rec + (size_t)c->rec_n * REC_STRIDE;
   c->rec_t.push_back(t);
@@ -179,6 +150,27 @@ double* next_record(mx_ctx* c, double t, long long step) {
 }
 
 template <typename T> using C2 = mx::cx<T>;
+
+// ------------------------------------------------------------ FFT autotuner
+//
+// Each FFT pass of a grid shape has a schedule: the persistent grid size in
+// blocks per SM (0 = one block per tile).  mx_autotune times the candidates
+// on the context's own buffers and keeps the fastest in a process-wide table
+// keyed by (pass, precision, grid shape); untuned passes use the default.
+enum Pass { P_X_R2C = 0, P_Y_FWD, P_Z_FWD, P_Z_INV, P_Y_INV, P_X_C2R, P_COUNT };
+constexpr int kCandidates[] = {0, 1, 2, 4, 8};
+constexpr int kDefaultBps = 4;
+std::mutex g_tune_mu;
+std::map<long long, int> g_tune;
+
+long long tune_key(const mx_ctx* c, int pass) {
+  return ((((long long)pass * 2 + c->prec) * 1024 + c->nx) * 1024 + c->ny) * 1024 + c->nz;
+}
+int pass_bps(const mx_ctx* c, int pass) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(tune_key(c, pass));
+  return it == g_tune.end() ? kDefaultBps : it->second;
+}
 
 // Event pair around one kernel launch when profiling is on.
 struct ProfScope {
@@ -213,16 +205,19 @@ cudaError_t forward3(mx_ctx* c, const T* e, const T* h, void* spec) {
   cudaError_t err;
   {
     ProfScope ps(c, MX_K_X_R2C);
-    err = mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, c->stream);
+    err = mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, pass_bps(c, P_X_R2C),
+                              c->stream);
   }
   if (err != cudaSuccess) return err;
   {
     ProfScope ps(c, MX_K_Y_FFT);
-    err = mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, c->stream);
+    err = mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, pass_bps(c, P_Y_FWD),
+                                c->stream);
   }
   if (err != cudaSuccess) return err;
   ProfScope ps(c, MX_K_Z_FFT);
-  return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, c->stream);
+  return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, pass_bps(c, P_Z_FWD),
+                               c->stream);
 }
 
 template <typename T>
@@ -232,17 +227,78 @@ cudaError_t inverse3(mx_ctx* c, void* spec, T* e, T* h) {
   cudaError_t err;
   {
     ProfScope ps(c, MX_K_Z_FFT);
-    err = mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, c->stream);
+    err = mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, pass_bps(c, P_Z_INV),
+                                c->stream);
   }
   if (err != cudaSuccess) return err;
   {
     ProfScope ps(c, MX_K_Y_FFT);
-    err = mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, c->stream);
+    err = mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, pass_bps(c, P_Y_INV),
+                                c->stream);
   }
   if (err != cudaSuccess) return err;
   const double scale = 1.0 / (double)c->ns;
   ProfScope ps(c, MX_K_X_C2R);
-  return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, scale, c->stream);
+  return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, scale, pass_bps(c, P_X_C2R),
+                             c->stream);
+}
+
+// One launch of `pass` with schedule bps on the context's work buffers (contents are scratch).
+template <typename T>
+cudaError_t run_pass(mx_ctx* c, int pass, int bps) {
+  const long long rows = (long long)c->ny * c->nz;
+  const size_t fb = (size_t)3 * c->ns * c->es;
+  T* e = (T*)c->phys;
+  T* h = (T*)((char*)c->phys + fb);
+  C2<T>* s = (C2<T>*)c->spec;
+  switch (pass) {
+    case P_X_R2C: return mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, bps, c->stream);
+    case P_Y_FWD: return mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream);
+    case P_Z_FWD:
+      return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream);
+    case P_Z_INV:
+      return mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream);
+    case P_Y_INV: return mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream);
+    case P_X_C2R:
+      return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, 1.0, bps, c->stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+mx_status tune_t(mx_ctx* c) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  MX_CHECK(c, cudaStreamIsCapturing(c->stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return MX_OK;  // never time inside a capture
+  // the passes below overwrite the work buffers: the spectral state at t_n is recomputed on demand
+  if (c->form == MX_FORM_LITERAL && c->loaded) return MX_OK;  // literal state lives in `phys`
+  cudaEvent_t e0, e1;
+  MX_CHECK(c, cudaEventCreate(&e0));
+  MX_CHECK(c, cudaEventCreate(&e1));
+  for (int pass = 0; pass < P_COUNT; ++pass) {
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      if (g_tune.count(tune_key(c, pass))) continue;
+    }
+    float best = 1e30f;
+    int best_bps = kDefaultBps;
+    for (int bps : kCandidates) {
+      MX_CHECK(c, run_pass<T>(c, pass, bps));  // warm-up (module load, attributes)
+      MX_CHECK(c, cudaEventRecord(e0, c->stream));
+      for (int r = 0; r < 3; ++r) MX_CHECK(c, run_pass<T>(c, pass, bps));
+      MX_CHECK(c, cudaEventRecord(e1, c->stream));
+      MX_CHECK(c, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      MX_CHECK(c, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) best = ms, best_bps = bps;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[tune_key(c, pass)] = best_bps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->spec_valid = false;
+  return MX_OK;
 }
 
 template <typename T>
@@ -497,6 +553,18 @@ mx_status mx_load_random_divfree(mx_ctx* c, unsigned long long seed, double sigm
   if (!c || !(sigma > 0.0) || !isfinite(sigma)) return MX_E_INVAL;
   if (c->err != MX_OK) return c->err;
   return c->prec == MX_FP64 ? load_random_t<double>(c, seed, sigma) : load_random_t<float>(c, seed, sigma);
+}
+
+mx_status mx_autotune(mx_ctx* c) {
+  if (!c) return MX_E_INVAL;
+  if (c->err != MX_OK) return c->err;
+  return c->prec == MX_FP64 ? tune_t<double>(c) : tune_t<float>(c);
+}
+
+mx_status mx_schedule(mx_ctx* c, int* bps, int n) {
+  if (!c || !bps || n < P_COUNT) return MX_E_INVAL;
+  for (int p = 0; p < P_COUNT; ++p) bps[p] = pass_bps(c, p);
+  return MX_OK;
 }
 
 mx_status mx_profile(mx_ctx* c, int enable) {

@@ -26,51 +26,61 @@ template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaSuccess;
 }
 
+// Grid of a persistent FFT launch: `bps` blocks per SM (0 = one block per work item).
+static long persistent_grid(long items, int bps) {
+  if (bps <= 0) return items;
+  const long cap = (long)num_sms() * bps;
+  return items < cap ? items : cap;
+}
+
 template <typename T, int M>
-static cudaError_t x_r2c_n(const T* e, const T* h, cx<T>* out, long rows3, long nrows, const twv<T>* tw, cudaStream_t s) {
+static cudaError_t x_r2c_n(const T* e, const T* h, cx<T>* out, long rows3, long nrows, const twv<T>* tw, int bps,
+                           cudaStream_t s) {
   constexpr int E = fft_E(M), TY = fft_TY(M), P = M / E;
   static_assert(plan_ok(M, E), "plan");
   const size_t smem = sizeof(twv<T>) * 2 * M + sizeof(cx<T>) * TY * (M + 1);
   auto k = k_x_r2c<T, M, E, TY>;
   cudaError_t err = set_smem(k, smem);
   if (err != cudaSuccess) return err;
-  const long blocks = (nrows + TY - 1) / TY;
+  const long blocks = persistent_grid((nrows + TY - 1) / TY, bps);
   k<<<(unsigned)blocks, P * TY, smem, s>>>(e, h, out, rows3, nrows, tw);
   return cudaGetLastError();
 }
 
 template <typename T, int M>
 static cudaError_t x_c2r_n(const cx<T>* in, T* e, T* h, long rows3, long nrows, const twv<T>* tw, double scale,
-                           cudaStream_t s) {
+                           int bps, cudaStream_t s) {
   constexpr int E = fft_E(M), TY = fft_TY(M), P = M / E;
   const size_t smem = sizeof(twv<T>) * 2 * M + sizeof(cx<T>) * TY * (M + 1);
   auto k = k_x_c2r<T, M, E, TY>;
   cudaError_t err = set_smem(k, smem);
   if (err != cudaSuccess) return err;
-  const long blocks = (nrows + TY - 1) / TY;
+  const long blocks = persistent_grid((nrows + TY - 1) / TY, bps);
   k<<<(unsigned)blocks, P * TY, smem, s>>>(in, e, h, rows3, nrows, tw, scale);
   return cudaGetLastError();
 }
 
 template <typename T, int N, int DIR>
-static cudaError_t strided_n(cx<T>* data, long inner, long outer, const twv<T>* tw, cudaStream_t s) {
+static cudaError_t strided_n(cx<T>* data, long inner, long outer, const twv<T>* tw, int bps, cudaStream_t s) {
   constexpr int E = fft_E(N), TX = fft_TX(N), P = N / E;
   static_assert(plan_ok(N, E), "plan");
   const size_t smem = sizeof(twv<T>) * N + sizeof(cx<T>) * N * TX;
   auto k = k_fft_strided<T, N, E, TX, DIR>;
   cudaError_t err = set_smem(k, smem);
   if (err != cudaSuccess) return err;
-  const long bx = (inner + TX - 1) / TX;
-  if (bx > 0x7fffffffL || outer > 65535) return cudaErrorInvalidConfiguration;
-  k<<<dim3((unsigned)bx, (unsigned)outer), P * TX, smem, s>>>(data, inner, tw);
+  const long tiles = (inner + TX - 1) / TX * outer;
+  const long blocks = persistent_grid(tiles, bps);
+  if (blocks > 0x7fffffffL) return cudaErrorInvalidConfiguration;
+  k<<<(unsigned)blocks, P * TX, smem, s>>>(data, inner, outer, tw);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_x_r2c(int M, const T* e, const T* h, cx<T>* out, long rows3, long nrows, const twv<T>* tw, cudaStream_t s) {
+cudaError_t launch_x_r2c(int M, const T* e, const T* h, cx<T>* out, long rows3, long nrows, const twv<T>* tw, int bps,
+                         cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   switch (M) {
-#define X(n) case n: return x_r2c_n<T, n>(e, h, out, rows3, nrows, tw, s);
+#define X(n) case n: return x_r2c_n<T, n>(e, h, out, rows3, nrows, tw, bps, s);
     MX_FOR_EACH_LEN(X)
 #undef X
   }
@@ -79,10 +89,10 @@ cudaError_t launch_x_r2c(int M, const T* e, const T* h, cx<T>* out, long rows3, 
 
 template <typename T>
 cudaError_t launch_x_c2r(int M, const cx<T>* in, T* e, T* h, long rows3, long nrows, const twv<T>* tw, double scale,
-                         cudaStream_t s) {
+                         int bps, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   switch (M) {
-#define X(n) case n: return x_c2r_n<T, n>(in, e, h, rows3, nrows, tw, scale, s);
+#define X(n) case n: return x_c2r_n<T, n>(in, e, h, rows3, nrows, tw, scale, bps, s);
     MX_FOR_EACH_LEN(X)
 #undef X
   }
@@ -90,17 +100,18 @@ cudaError_t launch_x_c2r(int M, const cx<T>* in, T* e, T* h, long rows3, long nr
 }
 
 template <typename T>
-cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const twv<T>* tw, cudaStream_t s) {
+cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const twv<T>* tw, int bps,
+                           cudaStream_t s) {
   if (inner <= 0 || outer <= 0 || N == 1) return cudaSuccess;
   if (dir < 0) {
     switch (N) {
-#define X(n) case n: return strided_n<T, n, -1>(data, inner, outer, tw, s);
+#define X(n) case n: return strided_n<T, n, -1>(data, inner, outer, tw, bps, s);
       MX_FOR_EACH_LEN(X)
 #undef X
     }
   } else {
     switch (N) {
-#define X(n) case n: return strided_n<T, n, +1>(data, inner, outer, tw, s);
+#define X(n) case n: return strided_n<T, n, +1>(data, inner, outer, tw, bps, s);
       MX_FOR_EACH_LEN(X)
 #undef X
     }

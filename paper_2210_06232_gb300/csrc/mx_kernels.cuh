@@ -269,6 +269,7 @@ __device__ __forceinline__ void reduce_and_finish(double* acc, double* __restric
 //   X_k = (Z_k + conj Z_{M-k})/2 + W_N^k (Z_k - conj Z_{M-k})/(2i),
 // and X_0 = Re Z_0 + Im Z_0, X_M = Re Z_0 - Im Z_0 packed as (X_0, X_M).
 // Rows 0 .. 3R-1 come from `in_e`, rows 3R .. 6R-1 from `in_h` (R = Ny Nz).
+// Persistent: a block loads the twiddles once and loops over groups of TY rows.
 template <typename T, int M, int E, int TY>
 __global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in_e, const T* __restrict__ in_h,
                                                         cx<T>* __restrict__ out, long rows3, long nrows,
@@ -281,39 +282,43 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in
   C* sm = reinterpret_cast<C*>(tw + 2 * M);
   for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) tw[i] = twg[i];
   const int t = threadIdx.x % P, ly = threadIdx.x / P;
-  const long row = (long)blockIdx.x * TY + ly;
-  const bool ok = row < nrows;
-  const T* src = ok ? (row < rows3 ? in_e + row * (2L * M) : in_h + (row - rows3) * (2L * M)) : nullptr;
-  C v[E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int n = t + P * m;
-    v[m] = ok ? *reinterpret_cast<const C*>(src + 2 * n) : C{0, 0};
-  }
-  __syncthreads();  // twiddles
   C* line = sm + ly * PITCH;
-  line_fft<T, M, E, -1>(v, line, 1, t, tw, 2);
-  __syncthreads();
+  const long ngroups = (nrows + TY - 1) / TY;
+  for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const long row = grp * TY + ly;
+    const bool ok = row < nrows;
+    const T* src = ok ? (row < rows3 ? in_e + row * (2L * M) : in_h + (row - rows3) * (2L * M)) : nullptr;
+    C v[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) line[t + P * m] = v[m];
-  __syncthreads();
-  if (!ok) return;
-  C* dst = out + row * M;
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int k = t + P * m;
-    C z = line[k];
-    C r;
-    if (k == 0) {
-      r = C{z.x + z.y, z.x - z.y};
-    } else {
-      C zp = cconj(line[M - k]);
-      C a = cadd(z, zp), d = csub(z, zp);   // 2A, 2iB
-      C b = C{d.y, -d.x};                    // 2B = -i * d
-      C wb = twmul<-1>(b, tw[k]);
-      r = C{(T)0.5 * (a.x + wb.x), (T)0.5 * (a.y + wb.y)};
+    for (int m = 0; m < E; ++m) {
+      const int n = t + P * m;
+      v[m] = ok ? *reinterpret_cast<const C*>(src + 2 * n) : C{0, 0};
     }
-    dst[k] = r;
+    __syncthreads();  // twiddles; previous group's readers of `line` are done
+    line_fft<T, M, E, -1>(v, line, 1, t, tw, 2);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) line[t + P * m] = v[m];
+    __syncthreads();
+    if (ok) {
+      C* dst = out + row * M;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int k = t + P * m;
+        C z = line[k];
+        C r;
+        if (k == 0) {
+          r = C{z.x + z.y, z.x - z.y};
+        } else {
+          C zp = cconj(line[M - k]);
+          C a = cadd(z, zp), d = csub(z, zp);  // 2A, 2iB
+          C b = C{d.y, -d.x};                   // 2B = -i * d
+          C wb = twmul<-1>(b, tw[k]);
+          r = C{(T)0.5 * (a.x + wb.x), (T)0.5 * (a.y + wb.y)};
+        }
+        dst[k] = r;
+      }
+    }
   }
 }
 
@@ -332,38 +337,43 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict_
   C* sm = reinterpret_cast<C*>(tw + 2 * M);
   for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) tw[i] = twg[i];
   const int t = threadIdx.x % P, ly = threadIdx.x / P;
-  const long row = (long)blockIdx.x * TY + ly;
-  const bool ok = row < nrows;
   C* line = sm + ly * PITCH;
-  const C* src = ok ? in + row * M : nullptr;
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int k = t + P * m;
-    line[k] = ok ? src[k] : C{0, 0};
-  }
-  __syncthreads();
-  C v[E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int k = t + P * m;
-    C x = line[k];
-    if (k == 0) {
-      v[m] = C{x.x + x.y, x.x - x.y};
-    } else {
-      C xp = cconj(line[M - k]);
-      C s = cadd(x, xp), d = csub(x, xp);
-      C wd = twmul<+1>(d, tw[k]);
-      v[m] = C{s.x - wd.y, s.y + wd.x};  // s + i * wd
-    }
-  }
-  line_fft<T, M, E, +1>(v, line, 1, t, tw, 2);
-  if (!ok) return;
-  T* dst = row < rows3 ? out_e + row * (2L * M) : out_h + (row - rows3) * (2L * M);
   const KC<T> sc(scale);  // 1/(Nx Ny Nz), hi + lo in FP32
+  const long ngroups = (nrows + TY - 1) / TY;
+  for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const long row = grp * TY + ly;
+    const bool ok = row < nrows;
+    const C* src = ok ? in + row * M : nullptr;
+    __syncthreads();  // twiddles; previous group's readers of `line` are done
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int n = t + P * m;
-    *reinterpret_cast<C*>(dst + 2 * n) = C{sc.mul(v[m].x), sc.mul(v[m].y)};
+    for (int m = 0; m < E; ++m) {
+      const int k = t + P * m;
+      line[k] = ok ? src[k] : C{0, 0};
+    }
+    __syncthreads();
+    C v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = t + P * m;
+      C x = line[k];
+      if (k == 0) {
+        v[m] = C{x.x + x.y, x.x - x.y};
+      } else {
+        C xp = cconj(line[M - k]);
+        C s = cadd(x, xp), d = csub(x, xp);
+        C wd = twmul<+1>(d, tw[k]);
+        v[m] = C{s.x - wd.y, s.y + wd.x};  // s + i * wd
+      }
+    }
+    line_fft<T, M, E, +1>(v, line, 1, t, tw, 2);
+    if (ok) {
+      T* dst = row < rows3 ? out_e + row * (2L * M) : out_h + (row - rows3) * (2L * M);
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int n = t + P * m;
+        *reinterpret_cast<C*>(dst + 2 * n) = C{sc.mul(v[m].x), sc.mul(v[m].y)};
+      }
+    }
   }
 }
 
@@ -371,9 +381,10 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict_
 //
 // data viewed as [outer][N][inner] complex; transforms every (outer, i)
 // line of N along the middle axis (y: inner = Mx; z: inner = Ny Mx).
-// Block = TX consecutive inner indices x P threads per line.
+// Tile = TX consecutive inner indices x P threads per line.  Persistent over
+// tiles (ntile_in tiles per outer index).
 template <typename T, int N, int E, int TX, int DIR>
-__global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict__ data, long inner,
+__global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict__ data, long inner, long outer,
                                                               const twv<T>* __restrict__ twg) {
   using C = cx<T>;
   constexpr int P = N / E;
@@ -382,17 +393,23 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
   C* sm = reinterpret_cast<C*>(tw + N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
   const int x = threadIdx.x % TX, t = threadIdx.x / TX;
-  const long col = (long)blockIdx.x * TX + x;
-  const bool ok = col < inner;
-  C* base = data + (long)blockIdx.y * N * inner + col;
-  C v[E];
+  const long ntile_in = (inner + TX - 1) / TX;
+  const long ntiles = ntile_in * outer;
+  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long o = tile / ntile_in;
+    const long col = (tile - o * ntile_in) * TX + x;
+    const bool ok = col < inner;
+    C* base = data + o * N * inner + col;
+    C v[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[m] = ok ? base[(long)(t + P * m) * inner] : C{0, 0};
-  __syncthreads();
-  line_fft<T, N, E, DIR>(v, sm + x, TX, t, tw, 1);
-  if (!ok) return;
+    for (int m = 0; m < E; ++m) v[m] = ok ? base[(long)(t + P * m) * inner] : C{0, 0};
+    __syncthreads();  // twiddles
+    line_fft<T, N, E, DIR>(v, sm + x, TX, t, tw, 1);
+    if (ok) {
 #pragma unroll
-  for (int m = 0; m < E; ++m) base[(long)(t + P * m) * inner] = v[m];
+      for (int m = 0; m < E; ++m) base[(long)(t + P * m) * inner] = v[m];
+    }
+  }
 }
 
 // ------------------------------------------------------ spectral update pass

@@ -10,16 +10,21 @@ namespace mx {
 // FFT lengths with a compiled plan: 2^a (1..512), 3*2^a (3..384), 5*2^a (5..320).
 bool fft_len_supported(int n);
 
+// Number of SMs of the current device (cached per process).
+int num_sms();
+
 // Twiddle tables: twv<T> entries exp(-2 pi i j / n) (FP32: hi + lo pairs).
+// bps: persistent grid of bps blocks per SM; 0 = one block per tile.
 template <typename T>
 cudaError_t launch_x_r2c(int M, const T* in_e, const T* in_h, cx<T>* out, long rows3, long nrows, const twv<T>* tw,
-                         cudaStream_t s);
+                         int bps, cudaStream_t s);
 template <typename T>
 cudaError_t launch_x_c2r(int M, const cx<T>* in, T* out_e, T* out_h, long rows3, long nrows, const twv<T>* tw,
-                         double scale, cudaStream_t s);
+                         double scale, int bps, cudaStream_t s);
 // dir = -1 forward, +1 inverse (unnormalised)
 template <typename T>
-cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const twv<T>* tw, cudaStream_t s);
+cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const twv<T>* tw, int bps,
+                           cudaStream_t s);
 
 // Spectral pass.  mode: 0 = invariants only, 1 = update only, 2 = update + invariants.
 // coef_kind: 0 = Coef<T> table, 1 = CoefHL table (float only), 2 = direct Coef<T>, 3 = direct CoefHL.

@@ -5,6 +5,18 @@
 
 namespace mx {
 
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      return 152;
+  }
+  return n;
+}
+
 int spectral_blocks(long npts) {
   // persistent-style grid: at most 2 blocks of 256 threads per SM of a 152-SM GB300
   long b = (npts + 511) / 512;

@@ -22,6 +22,12 @@ MX_FORM_LITERAL, MX_FORM_SPECTRAL = 0, 1
 KERNEL_KINDS = ("x_r2c", "x_c2r", "y_fft", "z_fft", "spectral", "table", "gen", "z_fused")
 
 
+class mx_instance_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("eps", C.c_double), ("mu", C.c_double), ("h", C.c_double)]
+
+
 class mx_invariants(C.Structure):
     _fields_ = [
         ("t", C.c_double), ("step", C.c_longlong),
@@ -57,6 +63,16 @@ def _load():
         "mx_time": (I, [P, C.POINTER(D), C.POINTER(LL)]),
         "mx_load_random_divfree": (I, [P, C.c_ulonglong, D]),
         "mx_profile": (I, [P, I]),
+        "mx_autotune": (I, [P]),
+        "mx_batch_create": (I, [C.POINTER(P), C.POINTER(mx_instance_desc), I, I, V]),
+        "mx_batch_size": (I, [P, C.POINTER(I)]),
+        "mx_batch_instance": (I, [P, I, C.POINTER(P)]),
+        "mx_batch_load_random": (I, [P, C.c_ulonglong, D]),
+        "mx_batch_step": (I, [P, LL, I]),
+        "mx_batch_sync": (I, [P]),
+        "mx_batch_graph_used": (I, [P, C.POINTER(I)]),
+        "mx_batch_destroy": (None, [P]),
+        "mx_schedule": (I, [P, C.POINTER(I), I]),
         "mx_spectral_update_noalloc": (I, [V, V, I, I, I, D3, D3, D, D, I, D, C.POINTER(mx_invariants), V]),
         "mx_profile_read": (I, [P, C.POINTER(D), C.POINTER(LL)]),
         "mx_sync": (I, [P]),
@@ -82,6 +98,16 @@ mx_read_invariants = _lib.mx_read_invariants
 mx_time = _lib.mx_time
 mx_load_random_divfree = _lib.mx_load_random_divfree
 mx_profile = _lib.mx_profile
+mx_autotune = _lib.mx_autotune
+mx_batch_create = _lib.mx_batch_create
+mx_batch_size = _lib.mx_batch_size
+mx_batch_instance = _lib.mx_batch_instance
+mx_batch_load_random = _lib.mx_batch_load_random
+mx_batch_step = _lib.mx_batch_step
+mx_batch_sync = _lib.mx_batch_sync
+mx_batch_graph_used = _lib.mx_batch_graph_used
+mx_batch_destroy = _lib.mx_batch_destroy
+mx_schedule = _lib.mx_schedule
 mx_spectral_update_noalloc = _lib.mx_spectral_update_noalloc
 mx_profile_read = _lib.mx_profile_read
 mx_sync = _lib.mx_sync
@@ -200,6 +226,14 @@ class Solver:
     def load_random(self, seed, sigma):
         check(mx_load_random_divfree(self._h, int(seed), float(sigma)), "mx_load_random_divfree")
 
+    def autotune(self):
+        check(mx_autotune(self._h), "mx_autotune")
+
+    def schedule(self):
+        arr = (C.c_int * 6)()
+        check(mx_schedule(self._h, arr, 6), "mx_schedule")
+        return list(arr)
+
     def profile(self, enable=True):
         check(mx_profile(self._h, 1 if enable else 0), "mx_profile")
 
@@ -218,3 +252,70 @@ class Solver:
 
     def sync(self):
         check(mx_sync(self._h), "mx_sync")
+
+
+class _Borrowed(Solver):
+    """A context owned by a batch: same methods as Solver, never destroyed here."""
+
+    def __init__(self, handle, n, precision):
+        self._h = handle
+        self.n = n
+        self.precision = precision
+        self.form = MX_FORM_SPECTRAL
+        self.dtype = np.float64 if precision == MX_FP64 else np.float32
+
+    def close(self):
+        self._h = C.c_void_p()
+
+
+class Batch:
+    """Independent spectral-form instances advanced by one persistent launch per step call."""
+
+    def __init__(self, instances, precision=MX_FP32, stream=None):
+        """instances: list of dicts with keys n=(nx,ny,nz), lo, hi, eps, mu, h."""
+        arr = (mx_instance_desc * len(instances))()
+        for i, d in enumerate(instances):
+            arr[i].nx, arr[i].ny, arr[i].nz = (int(v) for v in d["n"])
+            arr[i].lo = (C.c_double * 3)(*d.get("lo", (0.0, 0.0, 0.0)))
+            arr[i].hi = (C.c_double * 3)(*d.get("hi", (2 * np.pi,) * 3))
+            arr[i].eps, arr[i].mu, arr[i].h = float(d["eps"]), float(d["mu"]), float(d["h"])
+        h = C.c_void_p()
+        s = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        check(mx_batch_create(C.byref(h), arr, len(instances), int(precision), s), "mx_batch_create")
+        self._h = h
+        self.precision = precision
+        self.specs = [dict(d) for d in instances]
+
+    def __len__(self):
+        return len(self.specs)
+
+    def instance(self, i):
+        c = C.c_void_p()
+        check(mx_batch_instance(self._h, int(i), C.byref(c)), "mx_batch_instance")
+        return _Borrowed(c, tuple(int(v) for v in self.specs[i]["n"]), self.precision)
+
+    def load_random(self, seed, sigma):
+        check(mx_batch_load_random(self._h, int(seed), float(sigma)), "mx_batch_load_random")
+
+    def step(self, nsteps, invariants_every=1):
+        check(mx_batch_step(self._h, int(nsteps), int(invariants_every)), "mx_batch_step")
+
+    def sync(self):
+        check(mx_batch_sync(self._h), "mx_batch_sync")
+
+    def graph_used(self):
+        """1: replayed from a captured graph; 0: not yet; -e: capture refused with CUDA error e."""
+        v = C.c_int(0)
+        check(mx_batch_graph_used(self._h, C.byref(v)), "mx_batch_graph_used")
+        return v.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            mx_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
