@@ -276,6 +276,109 @@ def batch_run(torch, mx, peak, steps, warmup, stream, ninst=64, seed=4):
     }
 
 
+SERVE_SHAPES = [(32, 32, 32), (64, 64, 64), (96, 96, 96), (128, 128, 128), (192, 192, 192)]
+
+
+def serve_run(torch, mx, duration=5.0, rate=200.0, seed=5, budget=32 << 30):
+    """Serving form: Poisson arrivals (mean `rate`/s) of one-step solves (the paper's single step of size
+    t_end) with grids from SERVE_SHAPES, t_end ~ U[1, 50], eps, mu ~ U[1, 4], FP32 or FP64 (50/50), random
+    divergence-free initial fields; p50/p99 latency (submission to completion) and solves/s."""
+    import threading
+
+    rng = np.random.default_rng(seed)
+    inputs, outs = {}, {}
+    for sh in SERVE_SHAPES:
+        for prec in (mx.MX_FP32, mx.MX_FP64):
+            dt = torch.float64 if prec == mx.MX_FP64 else torch.float32
+            g = mx.Solver(sh, (0, 0, 0), (2 * np.pi,) * 3, 1.0, 1.0, prec, mx.MX_FORM_SPECTRAL)
+            g.load_random(seed + sh[0], 8.0)
+            E = torch.empty((3,) + sh, dtype=dt).pin_memory()
+            H = torch.empty_like(E).pin_memory()
+            g.read(E, H)
+            g.close()
+            inputs[(sh, prec)] = (E, H)
+            outs[(sh, prec)] = [(torch.empty_like(E).pin_memory(), torch.empty_like(H).pin_memory()) for _ in range(6)]
+    srv = mx.Server(budget, max_active=64)
+    free = {k: list(v) for k, v in outs.items()}
+    lock = threading.Lock()
+
+    def submit(sh, prec, t_end, eps, mu):
+        E0, H0 = inputs[(sh, prec)]
+        with lock:
+            pool = free[(sh, prec)]
+            Eo, Ho = pool.pop() if pool else (torch.empty_like(E0).pin_memory(), torch.empty_like(H0).pin_memory())
+        rid = srv.submit(sh, E0, H0, Eo, Ho, t_end, eps, mu, prec, 1, 0)
+        return rid, (sh, prec, Eo, Ho)
+
+    def release(tag):
+        sh, prec, Eo, Ho = tag
+        with lock:
+            free[(sh, prec)].append((Eo, Ho))
+
+    # warm-up: one request per class (creates and tunes the pooled contexts)
+    for sh in SERVE_SHAPES:
+        for prec in (mx.MX_FP32, mx.MX_FP64):
+            rid, tag = submit(sh, prec, 1.0, 1.0, 1.0)
+            srv.wait(rid)
+            srv.result(rid)
+            release(tag)
+    # arrivals
+    n = int(duration * rate)
+    gaps = rng.exponential(1.0 / rate, size=n)
+    plan = [(SERVE_SHAPES[rng.integers(len(SERVE_SHAPES))], mx.MX_FP32 if rng.random() < 0.5 else mx.MX_FP64,
+             float(rng.uniform(1, 50)), float(rng.uniform(1, 4)), float(rng.uniform(1, 4))) for _ in range(n)]
+    import queue as _q
+
+    pending = _q.Queue()
+    lat, done_t = [], []
+
+    def collector():  # waits in submission order, returns output buffers to the pool
+        while True:
+            item = pending.get()
+            if item is None:
+                return
+            rid, tag = item
+            if srv.wait(rid, 120.0) == 2:
+                _, l = srv.result(rid)
+                lat.append(l)
+                done_t.append(time.perf_counter())
+            release(tag)
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    due = t0
+    for gap, (sh, prec, t_end, eps, mu) in zip(gaps, plan):
+        due += gap
+        now = time.perf_counter()
+        if due > now:
+            time.sleep(due - now)
+        pending.put(submit(sh, prec, t_end, eps, mu))
+    t_sub = time.perf_counter()
+    pending.put(None)
+    th.join()
+    ok = len(lat)
+    t1 = max(done_t) if done_t else time.perf_counter()
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {
+        "requests": n,
+        "completed": ok,
+        "offered_rate_per_s": rate,
+        "solves_per_s": ok / (t1 - t0),
+        "arrival_window_s": t_sub - t0,
+        "p50_ms": float(np.percentile(lat, 50) * 1e3) if ok else None,
+        "p99_ms": float(np.percentile(lat, 99) * 1e3) if ok else None,
+        "mean_ms": float(lat.mean() * 1e3) if ok else None,
+        "hbm_budget_gb": budget / 1e9,
+        "hbm_high_water_gb": st["hbm_high_water"] / 1e9,
+        "rejected": st["rejected"],
+        "work": "one exponential step of size t_end per request (Sec. 2.5), load + solve + read through "
+                "pinned host buffers; grids 32^3..192^3, FP32/FP64 50/50, t_end ~ U[1,50]",
+    }
+
+
 def cpu_baseline_sample(budget_s=15.0):
     """The FP64 oracle (numpy, as it stands) on the host cores: Alg. 1 + Alg. 2 at 128^3."""
     import synth
@@ -430,6 +533,7 @@ def main():
 
     e2e = e2e_run(torch, mx, grid, args.steps, stream)
     batched = None if args.no_secondary else batch_run(torch, mx, peak, min(args.steps, 100), args.warmup, stream)
+    serve = None if (args.no_secondary or rank != 0) else serve_run(torch, mx)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline_sample()
@@ -476,6 +580,7 @@ def main():
         "clocks": ck,
         "forms": forms,
         "batched": batched,
+        "serve": serve,
     }
     print(json.dumps(out), flush=True)
     if dist is not None:

@@ -124,6 +124,15 @@ mx_status mx_load_fields(mx_ctx* ctx, const void* E, const void* H, int on_devic
 mx_status mx_step(mx_ctx* ctx, double h, long long nsteps, int invariants_every);
 
 /*
+ * Enqueue-only variants for host buffers that are pinned (page-locked):
+ * the copy, transform and record are placed on the context stream and the
+ * call returns without waiting; the host buffer must stay valid and
+ * unmodified (load) or unread (read) until mx_sync.
+ */
+mx_status mx_load_fields_async(mx_ctx* ctx, const void* E, const void* H);
+mx_status mx_read_fields_async(mx_ctx* ctx, void* E, void* H);
+
+/*
  * Write the fields at the current time (Def. 2.3 Step 4).
  *  E, H      : 3 x [Nz][Ny][Nx] each, element type of the precision.
  *  on_device : 0 = host pointers (the call waits for the copy), 1 = device
@@ -204,6 +213,57 @@ mx_status mx_batch_sync(mx_batch* b);
  * its own (the legacy default stream cannot be captured). */
 mx_status mx_batch_graph_used(mx_batch* b, int* used);
 void mx_batch_destroy(mx_batch* b);
+
+/*
+ * Serving form (no counterpart in the paper): a request loop that solves
+ * problems of different grids, domains, eps/mu, precisions and end times as
+ * they arrive.  A worker thread admits queued requests in arrival order while
+ * the HBM budget and `max_active` allow, each into a resident spectral-form
+ * context from a pool keyed by (precision, grid, domain) or newly created
+ * (idle pooled contexts are destroyed, least recently used first, when a new
+ * shape needs memory; the budget counts active and pooled contexts by
+ * mx_footprint_bytes).  Every context has its own CUDA stream, so requests
+ * admitted while others run overlap on the device.  A request runs
+ * mx_load_fields (host E0, H0), mx_step(t_end / nsteps, nsteps, ...) and
+ * mx_read_fields (host E_out, H_out); with nsteps = 1 it is the paper's
+ * single step of size t_end (Sec. 2.5).  Host buffers are borrowed until the
+ * request is done and should be pinned (page-locked): pageable buffers make
+ * the copies block the worker.  A request that can never fit the budget
+ * fails with MX_E_NOMEM.  Latency is completion minus submission (host
+ * steady clock).
+ */
+typedef struct mx_server mx_server;
+typedef struct {
+  int nx, ny, nz;
+  double lo[3], hi[3];
+  double eps, mu;
+  int precision;            /* MX_FP32 or MX_FP64 */
+  double t_end;             /* final time */
+  long long nsteps;         /* >= 1 steps of size t_end / nsteps */
+  int invariants_every;     /* record every k steps; 0: t = 0 and t_end only */
+  const void* E0;           /* host, 3 x [nz][ny][nx] of the precision */
+  const void* H0;
+  void* E_out;              /* host, receives the fields at t_end */
+  void* H_out;
+} mx_request;
+typedef struct {
+  long long submitted, admitted, completed, rejected, queued, active, pooled_contexts;
+  size_t hbm_in_use, hbm_high_water, hbm_budget;
+} mx_server_info;
+
+mx_status mx_server_create(mx_server** out, size_t hbm_budget_bytes, int max_active);
+mx_status mx_server_submit(mx_server* s, const mx_request* req, long long* id);
+/* state: 0 queued, 1 running, 2 done, < 0 failed with status -state. */
+mx_status mx_server_poll(mx_server* s, long long id, int* state);
+/* Wait up to timeout_s seconds; MX_E_TIMEOUT if the request is not done. */
+mx_status mx_server_wait(mx_server* s, long long id, double timeout_s, int* state);
+/* Invariant records (max == 0: count only) and latency of a done request;
+ * release != 0 forgets the request. */
+mx_status mx_server_result(mx_server* s, long long id, mx_invariants* inv, long long max, long long* n,
+                           double* latency_s, int release);
+mx_status mx_server_stats(mx_server* s, mx_server_info* out);
+/* Waits for running requests, then frees every context. */
+void mx_server_destroy(mx_server* s);
 
 /* Kernel classes timed by mx_profile. */
 typedef enum {

@@ -325,7 +325,7 @@ cudaError_t spectral_pass(mx_ctx* c, int mode, const void* src, void* dst, doubl
 }
 
 template <typename T>
-mx_status load_t(mx_ctx* c, const void* E, const void* H, int on_device) {
+mx_status load_t(mx_ctx* c, const void* E, const void* H, int on_device, bool wait = true) {
   const size_t fb = (size_t)3 * c->ns * c->es;
   const T *e = (const T*)E, *h = (const T*)H;
   if (!on_device || c->form == MX_FORM_LITERAL) {
@@ -343,7 +343,7 @@ mx_status load_t(mx_ctx* c, const void* E, const void* H, int on_device) {
   mx_status st = ensure_records(c, 1);
   if (st != MX_OK) return st;
   MX_CHECK(c, spectral_pass<T>(c, 0, target, nullptr, 0.0, next_record(c, 0.0, 0)));
-  if (!on_device) MX_CHECK(c, cudaStreamSynchronize(c->stream));
+  if (!on_device && wait) MX_CHECK(c, cudaStreamSynchronize(c->stream));
   c->t = 0.0;
   c->step = 0;
   c->loaded = true;
@@ -422,7 +422,7 @@ mx_status step_t(mx_ctx* c, double h, long long nsteps, int every) {
 }
 
 template <typename T>
-mx_status read_t(mx_ctx* c, void* E, void* H, int on_device) {
+mx_status read_t(mx_ctx* c, void* E, void* H, int on_device, bool wait = true) {
   const size_t fb = (size_t)3 * c->ns * c->es;
   if (c->form == MX_FORM_LITERAL) {
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -439,7 +439,7 @@ mx_status read_t(mx_ctx* c, void* E, void* H, int on_device) {
       MX_CHECK(c, cudaMemcpyAsync(H, (char*)c->phys + fb, fb, cudaMemcpyDeviceToHost, c->stream));
     }
   }
-  if (!on_device) MX_CHECK(c, cudaStreamSynchronize(c->stream));
+  if (!on_device && wait) MX_CHECK(c, cudaStreamSynchronize(c->stream));
   return MX_OK;
 }
 
@@ -547,6 +547,20 @@ mx_status mx_load_fields(mx_ctx* c, const void* E, const void* H, int on_device)
   if (!c || !E || !H) return MX_E_INVAL;
   if (c->err != MX_OK) return c->err;
   return c->prec == MX_FP64 ? load_t<double>(c, E, H, on_device) : load_t<float>(c, E, H, on_device);
+}
+
+// Host-buffer load and read that only enqueue (the caller waits on the stream):
+// used by the server, whose host buffers are pinned.
+mx_status mx_load_fields_async(mx_ctx* c, const void* E, const void* H) {
+  if (!c || !E || !H) return MX_E_INVAL;
+  if (c->err != MX_OK) return c->err;
+  return c->prec == MX_FP64 ? load_t<double>(c, E, H, 0, false) : load_t<float>(c, E, H, 0, false);
+}
+mx_status mx_read_fields_async(mx_ctx* c, void* E, void* H) {
+  if (!c || !E || !H) return MX_E_INVAL;
+  if (c->err != MX_OK) return c->err;
+  if (!c->loaded) return MX_E_STATE;
+  return c->prec == MX_FP64 ? read_t<double>(c, E, H, 0, false) : read_t<float>(c, E, H, 0, false);
 }
 
 mx_status mx_load_random_divfree(mx_ctx* c, unsigned long long seed, double sigma) {

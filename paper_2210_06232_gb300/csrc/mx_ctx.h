@@ -50,3 +50,4 @@ struct mx_ctx {
 
 // Grow the device record array so `more` records fit after the current ones.
 mx_status mx_ensure_records(mx_ctx* c, long long more);
+

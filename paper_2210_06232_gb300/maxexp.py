@@ -28,6 +28,21 @@ class mx_instance_desc(C.Structure):
                 ("eps", C.c_double), ("mu", C.c_double), ("h", C.c_double)]
 
 
+class mx_request(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("eps", C.c_double), ("mu", C.c_double), ("precision", C.c_int),
+                ("t_end", C.c_double), ("nsteps", C.c_longlong), ("invariants_every", C.c_int),
+                ("E0", C.c_void_p), ("H0", C.c_void_p), ("E_out", C.c_void_p), ("H_out", C.c_void_p)]
+
+
+class mx_server_info(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("admitted", C.c_longlong), ("completed", C.c_longlong),
+                ("rejected", C.c_longlong), ("queued", C.c_longlong), ("active", C.c_longlong),
+                ("pooled_contexts", C.c_longlong), ("hbm_in_use", C.c_size_t), ("hbm_high_water", C.c_size_t),
+                ("hbm_budget", C.c_size_t)]
+
+
 class mx_invariants(C.Structure):
     _fields_ = [
         ("t", C.c_double), ("step", C.c_longlong),
@@ -64,6 +79,15 @@ def _load():
         "mx_load_random_divfree": (I, [P, C.c_ulonglong, D]),
         "mx_profile": (I, [P, I]),
         "mx_autotune": (I, [P]),
+        "mx_load_fields_async": (I, [P, V, V]),
+        "mx_read_fields_async": (I, [P, V, V]),
+        "mx_server_create": (I, [C.POINTER(P), C.c_size_t, I]),
+        "mx_server_submit": (I, [P, C.POINTER(mx_request), C.POINTER(LL)]),
+        "mx_server_poll": (I, [P, LL, C.POINTER(I)]),
+        "mx_server_wait": (I, [P, LL, D, C.POINTER(I)]),
+        "mx_server_result": (I, [P, LL, C.POINTER(mx_invariants), LL, C.POINTER(LL), C.POINTER(D), I]),
+        "mx_server_stats": (I, [P, C.POINTER(mx_server_info)]),
+        "mx_server_destroy": (None, [P]),
         "mx_batch_create": (I, [C.POINTER(P), C.POINTER(mx_instance_desc), I, I, V]),
         "mx_batch_size": (I, [P, C.POINTER(I)]),
         "mx_batch_instance": (I, [P, I, C.POINTER(P)]),
@@ -99,6 +123,15 @@ mx_time = _lib.mx_time
 mx_load_random_divfree = _lib.mx_load_random_divfree
 mx_profile = _lib.mx_profile
 mx_autotune = _lib.mx_autotune
+mx_load_fields_async = _lib.mx_load_fields_async
+mx_read_fields_async = _lib.mx_read_fields_async
+mx_server_create = _lib.mx_server_create
+mx_server_submit = _lib.mx_server_submit
+mx_server_poll = _lib.mx_server_poll
+mx_server_wait = _lib.mx_server_wait
+mx_server_result = _lib.mx_server_result
+mx_server_stats = _lib.mx_server_stats
+mx_server_destroy = _lib.mx_server_destroy
 mx_batch_create = _lib.mx_batch_create
 mx_batch_size = _lib.mx_batch_size
 mx_batch_instance = _lib.mx_batch_instance
@@ -312,6 +345,76 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             mx_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (native worker thread in libmaxexp)."""
+
+    def __init__(self, hbm_budget_bytes, max_active=64):
+        h = C.c_void_p()
+        check(mx_server_create(C.byref(h), int(hbm_budget_bytes), int(max_active)), "mx_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, n, E0, H0, E_out, H_out, t_end, eps=1.0, mu=1.0, precision=MX_FP32, nsteps=1,
+               invariants_every=0, lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3):
+        """Host buffers (pinned torch tensors or numpy arrays) stay borrowed until the request is done."""
+        isz = 8 if precision == MX_FP64 else 4
+        cnt = 3 * int(n[0]) * int(n[1]) * int(n[2])
+        bufs = [_ptr(a, isz, cnt) for a in (E0, H0, E_out, H_out)]
+        if any(d for _, d in bufs):
+            raise ValueError("server requests take host buffers")
+        r = mx_request()
+        r.nx, r.ny, r.nz = (int(v) for v in n)
+        r.lo = (C.c_double * 3)(*lo)
+        r.hi = (C.c_double * 3)(*hi)
+        r.eps, r.mu, r.precision = float(eps), float(mu), int(precision)
+        r.t_end, r.nsteps, r.invariants_every = float(t_end), int(nsteps), int(invariants_every)
+        r.E0, r.H0, r.E_out, r.H_out = (b for b, _ in bufs)
+        rid = C.c_longlong(0)
+        check(mx_server_submit(self._h, C.byref(r), C.byref(rid)), "mx_server_submit")
+        self._keep[rid.value] = (E0, H0, E_out, H_out)
+        return rid.value
+
+    def poll(self, rid):
+        st = C.c_int(0)
+        check(mx_server_poll(self._h, int(rid), C.byref(st)), "mx_server_poll")
+        return st.value
+
+    def wait(self, rid, timeout=60.0):
+        st = C.c_int(0)
+        s = mx_server_wait(self._h, int(rid), float(timeout), C.byref(st))
+        if s not in (MX_OK, MX_E_TIMEOUT):
+            check(s, "mx_server_wait")
+        return st.value
+
+    def result(self, rid, release=True):
+        """(invariant records, latency in seconds) of a done request."""
+        n = C.c_longlong(0)
+        lat = C.c_double(0)
+        check(mx_server_result(self._h, int(rid), None, 0, C.byref(n), None, 0), "mx_server_result")
+        buf = (mx_invariants * max(1, n.value))()
+        check(mx_server_result(self._h, int(rid), buf, n.value, C.byref(n), C.byref(lat), 1 if release else 0),
+              "mx_server_result")
+        if release:
+            self._keep.pop(int(rid), None)
+        return [buf[i].as_dict() for i in range(n.value)], lat.value
+
+    def stats(self):
+        info = mx_server_info()
+        check(mx_server_stats(self._h, C.byref(info)), "mx_server_stats")
+        return {name: getattr(info, name) for name, _ in info._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            mx_server_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):
