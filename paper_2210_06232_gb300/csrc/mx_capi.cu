@@ -199,7 +199,7 @@ struct ProfScope {
 };
 
 template <typename T>
-cudaError_t forward3(mx_ctx* c, const T* e, const T* h, void* spec) {
+cudaError_t forward3(mx_ctx* c, const T* e, const T* h, void* spec, bool with_z = true) {
   const long long rows = (long long)c->ny * c->nz;
   C2<T>* s = (C2<T>*)spec;
   cudaError_t err;
@@ -214,18 +214,18 @@ cudaError_t forward3(mx_ctx* c, const T* e, const T* h, void* spec) {
     err = mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, pass_bps(c, P_Y_FWD),
                                 c->stream);
   }
-  if (err != cudaSuccess) return err;
+  if (err != cudaSuccess || !with_z) return err;
   ProfScope ps(c, MX_K_Z_FFT);
   return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, pass_bps(c, P_Z_FWD),
                                c->stream);
 }
 
 template <typename T>
-cudaError_t inverse3(mx_ctx* c, void* spec, T* e, T* h) {
+cudaError_t inverse3(mx_ctx* c, void* spec, T* e, T* h, bool with_z = true) {
   const long long rows = (long long)c->ny * c->nz;
   C2<T>* s = (C2<T>*)spec;
-  cudaError_t err;
-  {
+  cudaError_t err = cudaSuccess;
+  if (with_z) {
     ProfScope ps(c, MX_K_Z_FFT);
     err = mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, pass_bps(c, P_Z_INV),
                                 c->stream);
@@ -408,9 +408,23 @@ mx_status step_t(mx_ctx* c, double h, long long nsteps, int every) {
     if (c->form == MX_FORM_LITERAL) {
       T* e = (T*)c->phys;
       T* hh = (T*)((char*)c->phys + fb);
-      MX_CHECK(c, forward3<T>(c, e, hh, c->spec));
-      MX_CHECK(c, spectral_pass<T>(c, inv ? 2 : 1, c->spec, c->spec, h, record));
-      MX_CHECK(c, inverse3<T>(c, c->spec, e, hh));
+      if (mx::zfused_supported(c->nz, c->prec == MX_FP64)) {
+        // x, y forward; fused z forward -> update -> z inverse; y, x inverse: 5 passes
+        MX_CHECK(c, forward3<T>(c, e, hh, c->spec, false));
+        MX_CHECK(c, ensure_table<T>(c, h));
+        {
+          ProfScope ps(c, MX_K_ZFUSED);
+          const long tiles = (long)c->ny * ((c->mx + 3) / 4);
+          const int grid = (int)std::min<long>(std::max<long>(tiles, 1), c->pblocks);
+          MX_CHECK(c, mx::launch_z_fused<T>(coef_kind(c), (C2<T>*)c->spec, c->g, c->tab, h, (const mx::twv<T>*)c->twz,
+                                            grid, c->partials, c->counter, record, c->stream));
+        }
+        MX_CHECK(c, inverse3<T>(c, c->spec, e, hh, false));
+      } else {
+        MX_CHECK(c, forward3<T>(c, e, hh, c->spec));
+        MX_CHECK(c, spectral_pass<T>(c, inv ? 2 : 1, c->spec, c->spec, h, record));
+        MX_CHECK(c, inverse3<T>(c, c->spec, e, hh));
+      }
     } else {
       MX_CHECK(c, spectral_pass<T>(c, inv ? 2 : 1, c->spec0, c->spec, tn, record));
       c->spec_valid = true;
@@ -532,7 +546,9 @@ mx_status mx_create(mx_ctx** out, int nx, int ny, int nz, const double lo[3], co
   if (cudaMalloc(&c->spec, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
   if (form == MX_FORM_SPECTRAL && cudaMalloc(&c->spec0, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
   if (c->table && cudaMalloc(&c->tab, (size_t)c->nq * 32) != cudaSuccess) return fail(MX_E_NOMEM);
-  if (cudaMalloc(&c->partials, (size_t)c->sblocks * mx::NSUM * sizeof(double)) != cudaSuccess) return fail(MX_E_NOMEM);
+  // partial sums for up to 2 blocks per SM of any pass that reduces invariants
+  c->pblocks = std::max(c->sblocks, 2 * mx::num_sms());
+  if (cudaMalloc(&c->partials, (size_t)c->pblocks * mx::NSUM * sizeof(double)) != cudaSuccess) return fail(MX_E_NOMEM);
   if (cudaMalloc(&c->counter, 64) != cudaSuccess) return fail(MX_E_NOMEM);
   if (cudaMemset(c->counter, 0, 64) != cudaSuccess) return fail(MX_E_CUDA);
   if (upload_twiddles(c, nx, &c->twx) != cudaSuccess) return fail(MX_E_NOMEM);

@@ -29,6 +29,7 @@ struct mx_ctx {
   double* partials = nullptr;
   unsigned* counter = nullptr;
   int sblocks;
+  int pblocks;  // capacity of `partials` in blocks
   double* rec = nullptr;
   long long rec_cap = 0, rec_n = 0;
   std::vector<double> rec_t;

@@ -180,9 +180,16 @@ __host__ __device__ constexpr int num_stages(int N, int E) {
 // ------------------------------------------------------------------ the line FFT
 //
 // v      : E registers, v[m] <-> position t + P*m
-// sm     : this line's exchange buffer, position p at sm[p * SS]
+// sm     : this line's exchange buffer, position p at sm[xoff(p, SS)]:
+//          p * SS for interleaved lines (SS > 1); for a contiguous line
+//          (SS == 1) one complex of padding every 16, which spreads the
+//          stride-R exchange writes over all banks.
 // tw     : twiddle table, tw[j * TWS] = exp(-2 pi i j / N) for j < N (twv<T>)
 // All threads of the block must call this together (it synchronises).
+__device__ __forceinline__ int xoff(int p, int SS) { return SS == 1 ? p + (p >> 4) : p * SS; }
+// Exchange-buffer length (complex values) of one contiguous line of length n.
+__host__ __device__ constexpr int line_buf(int n) { return n + (n >> 4) + 1; }
+
 template <typename T, int N, int E, int DIR, int NS = 1>
 __device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, const twv<T>* tw, int TWS) {
   using C = cx<T>;
@@ -212,11 +219,11 @@ __device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, con
         const int k = j % NS;
         const int base = (j / NS) * NS * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) sm[(base + r * NS) * SS] = v[b + r * B];
+        for (int r = 0; r < R; ++r) sm[xoff(base + r * NS, SS)] = v[b + r * B];
       }
       __syncthreads();
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = sm[(t + P * m) * SS];
+      for (int m = 0; m < E; ++m) v[m] = sm[xoff(t + P * m, SS)];
       line_fft<T, N, E, DIR, NS * R>(v, sm, SS, t, tw, TWS);
     }
   }

@@ -38,7 +38,7 @@ static cudaError_t x_r2c_n(const T* e, const T* h, cx<T>* out, long rows3, long 
                            cudaStream_t s) {
   constexpr int E = fft_E(M), TY = fft_TY(M), P = M / E;
   static_assert(plan_ok(M, E), "plan");
-  const size_t smem = sizeof(twv<T>) * 2 * M + sizeof(cx<T>) * TY * (M + 1);
+  const size_t smem = sizeof(twv<T>) * 2 * M + sizeof(cx<T>) * TY * line_buf(M);
   auto k = k_x_r2c<T, M, E, TY>;
   cudaError_t err = set_smem(k, smem);
   if (err != cudaSuccess) return err;
@@ -51,7 +51,7 @@ template <typename T, int M>
 static cudaError_t x_c2r_n(const cx<T>* in, T* e, T* h, long rows3, long nrows, const twv<T>* tw, double scale,
                            int bps, cudaStream_t s) {
   constexpr int E = fft_E(M), TY = fft_TY(M), P = M / E;
-  const size_t smem = sizeof(twv<T>) * 2 * M + sizeof(cx<T>) * TY * (M + 1);
+  const size_t smem = sizeof(twv<T>) * 2 * M + sizeof(cx<T>) * TY * line_buf(M);
   auto k = k_x_c2r<T, M, E, TY>;
   cudaError_t err = set_smem(k, smem);
   if (err != cudaSuccess) return err;

@@ -276,7 +276,7 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in
                                                         const twv<T>* __restrict__ twg) {
   using C = cx<T>;
   constexpr int P = M / E;
-  constexpr int PITCH = M + 1;
+  constexpr int PITCH = line_buf(M);
   extern __shared__ __align__(16) unsigned char smraw[];
   twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);  // 2M entries: exp(-2 pi i j / (2M))
   C* sm = reinterpret_cast<C*>(tw + 2 * M);
@@ -298,19 +298,19 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in
     line_fft<T, M, E, -1>(v, line, 1, t, tw, 2);
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < E; ++m) line[t + P * m] = v[m];
+    for (int m = 0; m < E; ++m) line[xoff(t + P * m, 1)] = v[m];
     __syncthreads();
     if (ok) {
       C* dst = out + row * M;
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const int k = t + P * m;
-        C z = line[k];
+        C z = line[xoff(k, 1)];
         C r;
         if (k == 0) {
           r = C{z.x + z.y, z.x - z.y};
         } else {
-          C zp = cconj(line[M - k]);
+          C zp = cconj(line[xoff(M - k, 1)]);
           C a = cadd(z, zp), d = csub(z, zp);  // 2A, 2iB
           C b = C{d.y, -d.x};                   // 2B = -i * d
           C wb = twmul<-1>(b, tw[k]);
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict_
                                                         const twv<T>* __restrict__ twg, double scale) {
   using C = cx<T>;
   constexpr int P = M / E;
-  constexpr int PITCH = M + 1;
+  constexpr int PITCH = line_buf(M);
   extern __shared__ __align__(16) unsigned char smraw[];
   twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);
   C* sm = reinterpret_cast<C*>(tw + 2 * M);
@@ -348,18 +348,18 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict_
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int k = t + P * m;
-      line[k] = ok ? src[k] : C{0, 0};
+      line[xoff(k, 1)] = ok ? src[k] : C{0, 0};
     }
     __syncthreads();
     C v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int k = t + P * m;
-      C x = line[k];
+      C x = line[xoff(k, 1)];
       if (k == 0) {
         v[m] = C{x.x + x.y, x.x - x.y};
       } else {
-        C xp = cconj(line[M - k]);
+        C xp = cconj(line[xoff(M - k, 1)]);
         C s = cadd(x, xp), d = csub(x, xp);
         C wd = twmul<+1>(d, tw[k]);
         v[m] = C{s.x - wd.y, s.y + wd.x};  // s + i * wd
@@ -410,6 +410,90 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
       for (int m = 0; m < E; ++m) base[(long)(t + P * m) * inner] = v[m];
     }
   }
+}
+
+// ------------------------------------------------------- fused z pass (literal)
+//
+// For the literal form: the spectrum after the x and y passes is transformed
+// along z, multiplied by the exponential and transformed back, with all six
+// components of a tile (fixed ky, TX consecutive kx, every kz) held in
+// registers: thread (x, t) owns positions t + P*m of its column for the six
+// components, which are exactly the frequencies its forward transforms
+// produce and its inverse transforms consume (mx_fft.cuh).  One read and one
+// write of the spectrum replace three passes (z forward, update, z inverse).
+// Invariants of the updated state are summed as in the spectral pass.
+template <typename T, int N, int E, int TX, typename CoefT, bool INV>
+__global__ void __launch_bounds__((N / E) * TX) k_z_fused(cx<T>* __restrict__ data, GridParams g,
+                                                          const CoefT* __restrict__ tab, double tstep,
+                                                          const twv<T>* __restrict__ twg, double* __restrict__ partials,
+                                                          unsigned* __restrict__ counter, double* __restrict__ record) {
+  using C = cx<T>;
+  constexpr int P = N / E;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);
+  C* sm = reinterpret_cast<C*>(tw + N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  const int x = threadIdx.x % TX, t = threadIdx.x / TX;
+  const long inner = (long)g.mx * g.ny;  // stride between z planes
+  const long comp = inner * N;           // stride between components
+  const int ntx = (g.mx + TX - 1) / TX;
+  const long ntiles = (long)ntx * g.ny;
+  const T eps = (T)g.eps, mu = (T)g.mu;
+  const T nux = (T)g.nu[0], nuy = (T)g.nu[1], nuz = (T)g.nu[2];
+  double acc[INV ? NSUM : 1];
+  T part[INV ? NSUM : 1];
+#pragma unroll
+  for (int k = 0; k < (INV ? NSUM : 1); ++k) acc[k] = 0.0, part[k] = (T)0;
+  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int y = (int)(tile / ntx);
+    const int col = (int)(tile - (long)y * ntx) * TX + x;
+    const bool ok = col < g.mx;
+    C* base = data + (long)y * g.mx + col;
+    C v[6][E];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[c][m] = ok ? base[c * comp + (long)(t + P * m) * inner] : C{0, 0};
+    __syncthreads();  // twiddles
+#pragma unroll
+    for (int c = 0; c < 6; ++c) line_fft<T, N, E, -1>(v[c], sm + x, TX + 1, t, tw, 1);
+    if (ok) {
+      const int my = signed_index(y, g.ny);
+      const T kx = nux * (T)col, ky = nuy * (T)my;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int mz = signed_index(t + P * m, N);
+        const T kz = nuz * (T)mz;
+        CoefT q;
+        if (tab) {
+          q = tab[g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz];
+        } else {
+          const double k2 = g.nu[0] * g.nu[0] * (double)col * col + g.nu[1] * g.nu[1] * (double)my * my +
+                            g.nu[2] * g.nu[2] * (double)mz * mz;
+          q = coef_direct<T, CoefT>(k2, tstep, g);
+        }
+        C ee[3] = {v[0][m], v[1][m], v[2][m]};
+        C hh[3] = {v[3][m], v[4][m], v[5][m]};
+        Apply<T, CoefT>::run(q, kx, ky, kz, hh, ee);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c][m] = ee[c], v[c + 3][m] = hh[c];
+        if constexpr (INV) add_densities<T>(part, col == 0 ? (T)1 : (T)2, kx, ky, kz, hh, ee, eps, mu);
+      }
+      if constexpr (INV) {
+#pragma unroll
+        for (int k = 0; k < NSUM; ++k) acc[k] += (double)part[k], part[k] = (T)0;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) line_fft<T, N, E, +1>(v[c], sm + x, TX + 1, t, tw, 1);
+    if (ok) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) base[c * comp + (long)(t + P * m) * inner] = v[c][m];
+    }
+  }
+  if constexpr (INV) reduce_and_finish(acc, partials, counter, record);
 }
 
 // ------------------------------------------------------ spectral update pass

@@ -41,6 +41,15 @@ template <typename T>
 cudaError_t launch_gen_divfree(cx<T>* spec, long npts, const GridParams& g, unsigned long long seed, double sigma,
                                double amp, cudaStream_t s);
 
+// Fused z forward -> update (+ invariants when record != nullptr) -> z inverse
+// of the literal form, in place on a spectrum after the x and y passes.
+// coef_kind as for launch_spectral (table kinds need `tab`, direct kinds ignore it).
+bool zfused_supported(int nz, bool fp64);
+template <typename T>
+cudaError_t launch_z_fused(int coef_kind, cx<T>* data, const GridParams& g, const void* tab, double t,
+                           const twv<T>* tw, int grid, double* partials, unsigned* counter, double* record,
+                           cudaStream_t s);
+
 // Blocks used by the spectral pass for npts points (fixed per size: makes
 // the invariant reduction order independent of what else runs).
 int spectral_blocks(long npts);
