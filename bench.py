@@ -157,11 +157,18 @@ def timed_steps(torch, solver, stream, h, steps, warmup, dist=None, clocks=None)
 
 
 def max_over_ranks(torch, dist, v):
+    """Largest value over ranks (the slowest rank's time); NCCL reduces on the GPU, gloo on the host."""
     if dist is None:
         return v
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(world, units_per_rank, ms):
+    """Replicas: every rank processes units_per_rank; throughput = all units / slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
 
 
 def traffic_for(kernel):
@@ -511,7 +518,7 @@ def main():
                                     stream, dist, clocks)
     ms = max_over_ranks(torch, dist, ms)
     ns = grid ** 3
-    value = world * ns * args.steps / (ms / 1e3)
+    value = whole_job_value(world, ns * args.steps, ms)
     nh = ns // 2
     spec_ms, spec_n = prof["spectral"]
     bytes_per_launch = 12 * nh * 8  # read 6 complex FP32 components, write 6

@@ -284,16 +284,23 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in
   const int t = threadIdx.x % P, ly = threadIdx.x / P;
   C* line = sm + ly * PITCH;
   const long ngroups = (nrows + TY - 1) / TY;
+  // register double buffer: the next group's row values are requested before this group is transformed
+  auto load_group = [&](long grp, C* dst) {
+    const long row = grp * TY + ly;
+    const bool ok = grp < ngroups && row < nrows;
+    const T* src = ok ? (row < rows3 ? in_e + row * (2L * M) : in_h + (row - rows3) * (2L * M)) : nullptr;
+#pragma unroll
+    for (int m = 0; m < E; ++m) dst[m] = ok ? *reinterpret_cast<const C*>(src + 2 * (t + P * m)) : C{0, 0};
+  };
+  C nxt[E];
+  load_group(blockIdx.x, nxt);
   for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const long row = grp * TY + ly;
     const bool ok = row < nrows;
-    const T* src = ok ? (row < rows3 ? in_e + row * (2L * M) : in_h + (row - rows3) * (2L * M)) : nullptr;
     C v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int n = t + P * m;
-      v[m] = ok ? *reinterpret_cast<const C*>(src + 2 * n) : C{0, 0};
-    }
+    for (int m = 0; m < E; ++m) v[m] = nxt[m];
+    load_group(grp + gridDim.x, nxt);
     __syncthreads();  // twiddles; previous group's readers of `line` are done
     line_fft<T, M, E, -1>(v, line, 1, t, tw, 2);
     __syncthreads();
@@ -340,16 +347,22 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict_
   C* line = sm + ly * PITCH;
   const KC<T> sc(scale);  // 1/(Nx Ny Nz), hi + lo in FP32
   const long ngroups = (nrows + TY - 1) / TY;
+  auto load_group = [&](long grp, C* dst) {
+    const long row = grp * TY + ly;
+    const bool ok = grp < ngroups && row < nrows;
+    const C* src = ok ? in + row * M : nullptr;
+#pragma unroll
+    for (int m = 0; m < E; ++m) dst[m] = ok ? src[t + P * m] : C{0, 0};
+  };
+  C nxt[E];
+  load_group(blockIdx.x, nxt);
   for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const long row = grp * TY + ly;
     const bool ok = row < nrows;
-    const C* src = ok ? in + row * M : nullptr;
     __syncthreads();  // twiddles; previous group's readers of `line` are done
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int k = t + P * m;
-      line[xoff(k, 1)] = ok ? src[k] : C{0, 0};
-    }
+    for (int m = 0; m < E; ++m) line[xoff(t + P * m, 1)] = nxt[m];
+    load_group(grp + gridDim.x, nxt);
     __syncthreads();
     C v[E];
 #pragma unroll
@@ -395,6 +408,16 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
   const int x = threadIdx.x % TX, t = threadIdx.x / TX;
   const long ntile_in = (inner + TX - 1) / TX;
   const long ntiles = ntile_in * outer;
+  auto load_tile = [&](long tile, C* dst) {
+    const long o = tile / ntile_in;
+    const long col = (tile - o * ntile_in) * TX + x;
+    const bool ok = tile < ntiles && col < inner;
+    const C* b = data + o * N * inner + col;
+#pragma unroll
+    for (int m = 0; m < E; ++m) dst[m] = ok ? b[(long)(t + P * m) * inner] : C{0, 0};
+  };
+  C nxt[E];
+  load_tile(blockIdx.x, nxt);
   for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long o = tile / ntile_in;
     const long col = (tile - o * ntile_in) * TX + x;
@@ -402,7 +425,9 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
     C* base = data + o * N * inner + col;
     C v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = ok ? base[(long)(t + P * m) * inner] : C{0, 0};
+    for (int m = 0; m < E; ++m) v[m] = nxt[m];
+    // in place: the next tile is another set of columns, never written by this tile
+    load_tile(tile + gridDim.x, nxt);
     __syncthreads();  // twiddles
     line_fft<T, N, E, DIR>(v, sm + x, TX, t, tw, 1);
     if (ok) {
