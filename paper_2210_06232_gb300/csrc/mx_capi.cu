@@ -206,7 +206,7 @@ cudaError_t forward3(mx_ctx* c, const T* e, const T* h, void* spec, bool with_z 
   {
     ProfScope ps(c, MX_K_X_R2C);
     err = mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, pass_bps(c, P_X_R2C),
-                              c->stream);
+                              c->stream, c->counter);
   }
   if (err != cudaSuccess) return err;
   {
@@ -240,7 +240,7 @@ cudaError_t inverse3(mx_ctx* c, void* spec, T* e, T* h, bool with_z = true) {
   const double scale = 1.0 / (double)c->ns;
   ProfScope ps(c, MX_K_X_C2R);
   return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, scale, pass_bps(c, P_X_C2R),
-                             c->stream);
+                             c->stream, c->counter);
 }
 
 // One launch of `pass` with schedule bps on the context's work buffers (contents are scratch).
@@ -252,7 +252,8 @@ cudaError_t run_pass(mx_ctx* c, int pass, int bps) {
   T* h = (T*)((char*)c->phys + fb);
   C2<T>* s = (C2<T>*)c->spec;
   switch (pass) {
-    case P_X_R2C: return mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, bps, c->stream);
+    case P_X_R2C:
+      return mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, bps, c->stream, c->counter);
     case P_Y_FWD: return mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream);
     case P_Z_FWD:
       return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream);
@@ -260,7 +261,8 @@ cudaError_t run_pass(mx_ctx* c, int pass, int bps) {
       return mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream);
     case P_Y_INV: return mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream);
     case P_X_C2R:
-      return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, 1.0, bps, c->stream);
+      return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, 1.0, bps, c->stream,
+                                 c->counter);
   }
   return cudaErrorInvalidValue;
 }

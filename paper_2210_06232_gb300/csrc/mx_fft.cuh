@@ -185,12 +185,19 @@ __host__ __device__ constexpr int num_stages(int N, int E) {
 //          (SS == 1) one complex of padding every 16, which spreads the
 //          stride-R exchange writes over all banks.
 // tw     : twiddle table, tw[j * TWS] = exp(-2 pi i j / N) for j < N (twv<T>)
-// All threads of the block must call this together (it synchronises).
+// All threads of the block must call this together (it synchronises):
+// NBAR == 0 uses __syncthreads(); NBAR > 0 uses named barrier 1 over the
+// first NBAR threads (warp-specialised kernels whose producer warp is busy).
 __device__ __forceinline__ int xoff(int p, int SS) { return SS == 1 ? p + (p >> 4) : p * SS; }
 // Exchange-buffer length (complex values) of one contiguous line of length n.
 __host__ __device__ constexpr int line_buf(int n) { return n + (n >> 4) + 1; }
 
-template <typename T, int N, int E, int DIR, int NS = 1>
+template <int NBAR> __device__ __forceinline__ void fft_bar() {
+  if constexpr (NBAR == 0) __syncthreads();
+  else asm volatile("bar.sync 1, %0;" ::"r"(NBAR) : "memory");
+}
+
+template <typename T, int N, int E, int DIR, int NBAR = 0, int NS = 1>
 __device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, const twv<T>* tw, int TWS) {
   using C = cx<T>;
   if constexpr (NS < N) {
@@ -212,7 +219,7 @@ __device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, con
       bfly<R, DIR, B>(v + b);
     }
     if constexpr (NS * R < N) {
-      __syncthreads();  // previous readers of sm are done
+      fft_bar<NBAR>();  // previous readers of sm are done
 #pragma unroll
       for (int b = 0; b < B; ++b) {
         const int j = t + P * b;
@@ -221,10 +228,10 @@ __device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, con
 #pragma unroll
         for (int r = 0; r < R; ++r) sm[xoff(base + r * NS, SS)] = v[b + r * B];
       }
-      __syncthreads();
+      fft_bar<NBAR>();
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = sm[xoff(t + P * m, SS)];
-      line_fft<T, N, E, DIR, NS * R>(v, sm, SS, t, tw, TWS);
+      line_fft<T, N, E, DIR, NBAR, NS * R>(v, sm, SS, t, tw, TWS);
     }
   }
 }

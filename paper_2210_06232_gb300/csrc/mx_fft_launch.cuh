@@ -2,6 +2,7 @@
 // mx_fft_f32.cu and mx_fft_f64.cu.
 #pragma once
 #include "mx_launch.h"
+#include "mx_xpass_tma.cuh"
 
 namespace mx {
 
@@ -33,11 +34,30 @@ static long persistent_grid(long items, int bps) {
   return items < cap ? items : cap;
 }
 
+// Bulk-copy pipelined x passes: rows of at least 32 complex values, groups that
+// never straddle the E/H boundary, 16-byte aligned buffers.
+template <typename T, int M>
+static bool xp_tma_ok(const void* a, const void* b, long rows3) {
+  constexpr int TY = fft_TY(M);
+  return M >= 32 && rows3 % TY == 0 && ((((uintptr_t)a) | ((uintptr_t)b)) & 15u) == 0;
+}
+
 template <typename T, int M>
 static cudaError_t x_r2c_n(const T* e, const T* h, cx<T>* out, long rows3, long nrows, const twv<T>* tw, int bps,
-                           cudaStream_t s) {
+                           cudaStream_t s, unsigned* counter) {
   constexpr int E = fft_E(M), TY = fft_TY(M), P = M / E;
   static_assert(plan_ok(M, E), "plan");
+  if constexpr (M >= 32 && xp_fits<T, M, TY>()) {
+    if (counter && xp_tma_ok<T, M>(e, h, rows3)) {
+      const size_t smem = xp_smem<T, M, TY>();
+      auto k = k_x_r2c_tma<T, M, E, TY>;
+      cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+      const long blocks = persistent_grid((nrows + TY - 1) / TY, bps > 0 ? bps : 2);
+      k<<<(unsigned)blocks, P * TY + 32, smem, s>>>(e, h, out, rows3, nrows, tw, counter);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = sizeof(twv<T>) * 2 * M + sizeof(cx<T>) * TY * line_buf(M);
   auto k = k_x_r2c<T, M, E, TY>;
   cudaError_t err = set_smem(k, smem);
@@ -49,8 +69,19 @@ static cudaError_t x_r2c_n(const T* e, const T* h, cx<T>* out, long rows3, long 
 
 template <typename T, int M>
 static cudaError_t x_c2r_n(const cx<T>* in, T* e, T* h, long rows3, long nrows, const twv<T>* tw, double scale,
-                           int bps, cudaStream_t s) {
+                           int bps, cudaStream_t s, unsigned* counter) {
   constexpr int E = fft_E(M), TY = fft_TY(M), P = M / E;
+  if constexpr (M >= 32 && xp_fits<T, M, TY>()) {
+    if (counter && xp_tma_ok<T, M>(in, in, rows3)) {
+      const size_t smem = xp_smem<T, M, TY>();
+      auto k = k_x_c2r_tma<T, M, E, TY>;
+      cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+      const long blocks = persistent_grid((nrows + TY - 1) / TY, bps > 0 ? bps : 2);
+      k<<<(unsigned)blocks, P * TY + 32, smem, s>>>(in, e, h, rows3, nrows, tw, scale, counter);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = sizeof(twv<T>) * 2 * M + sizeof(cx<T>) * TY * line_buf(M);
   auto k = k_x_c2r<T, M, E, TY>;
   cudaError_t err = set_smem(k, smem);
@@ -77,10 +108,10 @@ static cudaError_t strided_n(cx<T>* data, long inner, long outer, const twv<T>* 
 
 template <typename T>
 cudaError_t launch_x_r2c(int M, const T* e, const T* h, cx<T>* out, long rows3, long nrows, const twv<T>* tw, int bps,
-                         cudaStream_t s) {
+                         cudaStream_t s, unsigned* counter) {
   if (nrows <= 0) return cudaSuccess;
   switch (M) {
-#define X(n) case n: return x_r2c_n<T, n>(e, h, out, rows3, nrows, tw, bps, s);
+#define X(n) case n: return x_r2c_n<T, n>(e, h, out, rows3, nrows, tw, bps, s, counter);
     MX_FOR_EACH_LEN(X)
 #undef X
   }
@@ -89,10 +120,10 @@ cudaError_t launch_x_r2c(int M, const T* e, const T* h, cx<T>* out, long rows3, 
 
 template <typename T>
 cudaError_t launch_x_c2r(int M, const cx<T>* in, T* e, T* h, long rows3, long nrows, const twv<T>* tw, double scale,
-                         int bps, cudaStream_t s) {
+                         int bps, cudaStream_t s, unsigned* counter) {
   if (nrows <= 0) return cudaSuccess;
   switch (M) {
-#define X(n) case n: return x_c2r_n<T, n>(in, e, h, rows3, nrows, tw, scale, bps, s);
+#define X(n) case n: return x_c2r_n<T, n>(in, e, h, rows3, nrows, tw, scale, bps, s, counter);
     MX_FOR_EACH_LEN(X)
 #undef X
   }

@@ -15,12 +15,14 @@ int num_sms();
 
 // Twiddle tables: twv<T> entries exp(-2 pi i j / n) (FP32: hi + lo pairs).
 // bps: persistent grid of bps blocks per SM; 0 = one block per tile.
+// counter: the context's block counter (counter[1] = wait-timeout flag); with
+// counter != nullptr rows of >= 32 complex values use the bulk-copy pipeline.
 template <typename T>
 cudaError_t launch_x_r2c(int M, const T* in_e, const T* in_h, cx<T>* out, long rows3, long nrows, const twv<T>* tw,
-                         int bps, cudaStream_t s);
+                         int bps, cudaStream_t s, unsigned* counter = nullptr);
 template <typename T>
 cudaError_t launch_x_c2r(int M, const cx<T>* in, T* out_e, T* out_h, long rows3, long nrows, const twv<T>* tw,
-                         double scale, int bps, cudaStream_t s);
+                         double scale, int bps, cudaStream_t s, unsigned* counter = nullptr);
 // dir = -1 forward, +1 inverse (unnormalised)
 template <typename T>
 cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const twv<T>* tw, int bps,
