@@ -315,8 +315,10 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_batch_steps(BatchArgs a) {
         const unsigned p0 = (gc - b.chunk0) * CH;
         const long long N = b.n0 + n;
         const bool rec = recorded(b, N);
-        if (!mbar_wait_bounded(&full[s], (ii / BT_NST) & 1u)) {
-          atomicExch(a.bar + 2, 1u);
+        // the warp leaves together (its lanes meet again in warp shuffles)
+        const bool lost = !mbar_wait_bounded(&full[s], (ii / BT_NST) & 1u);
+        if (__any_sync(0xffffffffu, lost)) {
+          if (lost) atomicExch(a.bar + 2, 1u);
           break;
         }
         C v[6][PPT];

@@ -68,10 +68,60 @@ void twiddles(int n, std::vector<double>& re, std::vector<double>& im) {
   }
 }
 
+// Appends the stage-major twiddle table of the length-n line FFT with E values per
+// thread (mx::tw_stage_off): stage (NS, R), entry [r-1][k] = exp(-2 pi i r k / (NS R)).
+void stage_twiddles(int n, int E, std::vector<double>& re, std::vector<double>& im) {
+  std::vector<double> wr, wi;
+  twiddles(n, wr, wi);
+  for (int ns = 1; ns < n;) {
+    const int r = mx::pick_radix(n / ns, E);
+    if (r <= 0) return;
+    if (ns > 1)
+      for (int q = 1; q < r; ++q)
+        for (int k = 0; k < ns; ++k) {
+          const long j = ((long)q * k * (n / (ns * r))) % n;
+          re.push_back(wr[j]);
+          im.push_back(wi[j]);
+        }
+    ns *= r;
+  }
+}
+
+// Per-axis tables of the FFT kernels:
+//   x (line of nx reals = M = nx/2 complex): exp(-2 pi i k / nx) for k < M (packing),
+//     then the stage table of the M-point FFT;
+//   y: the stage table of the ny-point FFT;
+//   z: the stage table of the nz-point FFT, then that of the fused z pass's plan
+//     (starting at entry *zf_off).
+void axis_twiddles(int axis, int n, bool fp64, std::vector<double>& re, std::vector<double>& im, int* zf_off) {
+  re.clear();
+  im.clear();
+  if (axis == 0) {
+    const int M = n / 2;
+    std::vector<double> wr, wi;
+    twiddles(n, wr, wi);
+    re.assign(wr.begin(), wr.begin() + M);
+    im.assign(wi.begin(), wi.begin() + M);
+    stage_twiddles(M, mx::fft_line_E(M), re, im);
+    return;
+  }
+  stage_twiddles(n, mx::fft_line_E(n), re, im);
+  if (axis == 2) {
+    *zf_off = (int)re.size();
+    const int ez = mx::zfused_line_E(n, fp64);
+    if (ez > 0) stage_twiddles(n, ez, re, im);
+  }
+}
+
 // FP64: double2 per entry.  FP32: float4 (hi.x, hi.y, lo.x, lo.y) with value = hi + lo.
-cudaError_t upload_twiddles(mx_ctx* c, int n, void** dst) {
+cudaError_t upload_twiddles(mx_ctx* c, int axis, int n, void** dst) {
   std::vector<double> re, im;
-  twiddles(n, re, im);
+  int zf_off = 0;
+  axis_twiddles(axis, n, c->prec == MX_FP64, re, im, &zf_off);
+  if (axis == 2) c->twz_zf = zf_off;
+  n = std::max<int>(1, (int)re.size());
+  re.resize(n, 1.0);
+  im.resize(n, 0.0);
   if (c->prec == MX_FP64) {
     cudaError_t e = cudaMalloc(dst, (size_t)n * sizeof(double2));
     if (e != cudaSuccess) return e;
@@ -418,7 +468,7 @@ mx_status step_t(mx_ctx* c, double h, long long nsteps, int every) {
           ProfScope ps(c, MX_K_ZFUSED);
           const long tiles = (long)c->ny * ((c->mx + 3) / 4);
           const int grid = (int)std::min<long>(std::max<long>(tiles, 1), c->pblocks);
-          MX_CHECK(c, mx::launch_z_fused<T>(coef_kind(c), (C2<T>*)c->spec, c->g, c->tab, h, (const mx::twv<T>*)c->twz,
+          MX_CHECK(c, mx::launch_z_fused<T>(coef_kind(c), (C2<T>*)c->spec, c->g, c->tab, h, (const mx::twv<T>*)c->twz + c->twz_zf,
                                             grid, c->partials, c->counter, record, c->stream));
         }
         MX_CHECK(c, inverse3<T>(c, c->spec, e, hh, false));
@@ -466,7 +516,7 @@ size_t footprint(int nx, int ny, int nz, int prec, int form, int nq) {
   b += 6 * ns * es;                        // spec (nh complex == ns reals)
   if (form == MX_FORM_SPECTRAL) b += 6 * ns * es;  // spec0
   b += (size_t)nq * 32;                    // table
-  b += (size_t)(nx + ny + nz) * 2 * es;    // twiddles
+  b += (size_t)(nx + ny + 2 * nz) * 16;   // twiddles (16-byte entries)
   b += (size_t)152 * 4 * 16 * sizeof(double) + 64 * REC_STRIDE * sizeof(double) + 256;
   return b;
 }
@@ -553,9 +603,9 @@ mx_status mx_create(mx_ctx** out, int nx, int ny, int nz, const double lo[3], co
   if (cudaMalloc(&c->partials, (size_t)c->pblocks * mx::NSUM * sizeof(double)) != cudaSuccess) return fail(MX_E_NOMEM);
   if (cudaMalloc(&c->counter, 64) != cudaSuccess) return fail(MX_E_NOMEM);
   if (cudaMemset(c->counter, 0, 64) != cudaSuccess) return fail(MX_E_CUDA);
-  if (upload_twiddles(c, nx, &c->twx) != cudaSuccess) return fail(MX_E_NOMEM);
-  if (upload_twiddles(c, ny, &c->twy) != cudaSuccess) return fail(MX_E_NOMEM);
-  if (upload_twiddles(c, nz, &c->twz) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (upload_twiddles(c, 0, nx, &c->twx) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (upload_twiddles(c, 1, ny, &c->twy) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (upload_twiddles(c, 2, nz, &c->twz) != cudaSuccess) return fail(MX_E_NOMEM);
   if (ensure_records(c, 64) != MX_OK) return fail(MX_E_NOMEM);
   *out = c;
   return MX_OK;

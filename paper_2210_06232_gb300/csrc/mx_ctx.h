@@ -26,6 +26,7 @@ struct mx_ctx {
   void* twx = nullptr;
   void* twy = nullptr;
   void* twz = nullptr;
+  int twz_zf = 0;  // entry of twz where the fused z pass's table starts
   double* partials = nullptr;
   unsigned* counter = nullptr;
   int sblocks;

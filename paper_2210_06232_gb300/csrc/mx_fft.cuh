@@ -177,6 +177,21 @@ __host__ __device__ constexpr int num_stages(int N, int E) {
   return s;
 }
 
+// Stage-major twiddle table of a line FFT of length N with E values per thread:
+// for each stage after the first (NS > 1, radix R) the entries
+// [r - 1][k] = exp(-2 pi i r k / (NS R)), r = 1..R-1, k = 0..NS-1, so that the
+// threads of a warp (consecutive k) read consecutive entries.
+__host__ __device__ constexpr int tw_stage_off(int N, int E, int NS) {
+  int off = 0, ns = 1;
+  while (ns < NS) {
+    const int r = pick_radix(N / ns, E);
+    if (ns > 1) off += ns * (r - 1);
+    ns *= r;
+  }
+  return off;
+}
+__host__ __device__ constexpr int tw_len(int N, int E) { return tw_stage_off(N, E, N); }
+
 // ------------------------------------------------------------------ the line FFT
 //
 // v      : E registers, v[m] <-> position t + P*m
@@ -184,21 +199,45 @@ __host__ __device__ constexpr int num_stages(int N, int E) {
 //          p * SS for interleaved lines (SS > 1); for a contiguous line
 //          (SS == 1) one complex of padding every 16, which spreads the
 //          stride-R exchange writes over all banks.
-// tw     : twiddle table, tw[j * TWS] = exp(-2 pi i j / N) for j < N (twv<T>)
-// All threads of the block must call this together (it synchronises):
-// NBAR == 0 uses __syncthreads(); NBAR > 0 uses named barrier 1 over the
-// first NBAR threads (warp-specialised kernels whose producer warp is busy).
+// tw     : stage-major twiddle table of (N, E) (tw_stage_off), twv<T> entries
+// All threads sharing the barrier must call this together (it synchronises):
+// NBAR < 0 uses __syncwarp() (each line within one warp), NBAR == 0
+// __syncthreads(), NBAR > 0 named barrier 1 over the first NBAR threads
+// (warp-specialised kernels whose producer warp is busy).
 __device__ __forceinline__ int xoff(int p, int SS) { return SS == 1 ? p + (p >> 4) : p * SS; }
 // Exchange-buffer length (complex values) of one contiguous line of length n.
 __host__ __device__ constexpr int line_buf(int n) { return n + (n >> 4) + 1; }
 
+// Barrier kinds: NBAR < 0 when every line lies within one warp (P threads per
+// line with P dividing 32): __syncwarp; 0: __syncthreads; > 0: named barrier 1
+// over the first NBAR threads.
 template <int NBAR> __device__ __forceinline__ void fft_bar() {
-  if constexpr (NBAR == 0) __syncthreads();
+  if constexpr (NBAR < 0) __syncwarp();
+  else if constexpr (NBAR == 0) __syncthreads();
   else asm volatile("bar.sync 1, %0;" ::"r"(NBAR) : "memory");
 }
+// The same synchronisation, returning whether any participating thread had `v` set
+// (a uniform decision, e.g. to leave a loop together).
+template <int NBAR> __device__ __forceinline__ bool fft_any(bool v) {
+  if constexpr (NBAR < 0) {
+    return __any_sync(0xffffffffu, v);
+  } else if constexpr (NBAR == 0) {
+    return __syncthreads_or(v) != 0;
+  } else {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(NBAR)
+        : "memory");
+    return r != 0;
+  }
+}
+// Barrier kind for lines of P threads in blocks whose consumers synchronise with `wide`.
+__host__ __device__ constexpr int line_bar(int P, int wide) { return (P <= 32 && 32 % P == 0) ? -1 : wide; }
 
 template <typename T, int N, int E, int DIR, int NBAR = 0, int NS = 1>
-__device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, const twv<T>* tw, int TWS) {
+__device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, const twv<T>* tw) {
   using C = cx<T>;
   if constexpr (NS < N) {
     constexpr int P = N / E;
@@ -211,10 +250,8 @@ __device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, con
       const int k = j % NS;
       if constexpr (NS > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const int widx = (r * k) * (N / (NS * R));
-          v[b + r * B] = twmul<DIR>(v[b + r * B], tw[widx * TWS]);
-        }
+        constexpr int OFF = tw_stage_off(N, E, NS);
+        for (int r = 1; r < R; ++r) v[b + r * B] = twmul<DIR>(v[b + r * B], tw[OFF + (r - 1) * NS + k]);
       }
       bfly<R, DIR, B>(v + b);
     }
@@ -231,7 +268,7 @@ __device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, con
       fft_bar<NBAR>();
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = sm[xoff(t + P * m, SS)];
-      line_fft<T, N, E, DIR, NBAR, NS * R>(v, sm, SS, t, tw, TWS);
+      line_fft<T, N, E, DIR, NBAR, NS * R>(v, sm, SS, t, tw);
     }
   }
 }

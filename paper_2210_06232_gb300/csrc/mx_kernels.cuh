@@ -277,10 +277,12 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in
   using C = cx<T>;
   constexpr int P = M / E;
   constexpr int PITCH = line_buf(M);
+  constexpr int LB = line_bar(P, 0);  // lines within a warp synchronise with __syncwarp
   extern __shared__ __align__(16) unsigned char smraw[];
-  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);  // 2M entries: exp(-2 pi i j / (2M))
+  // twiddles: exp(-2 pi i k / (2M)) for k < M (packing), then the stage-major table of the M-point FFT
+  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);
   C* sm = reinterpret_cast<C*>(tw + 2 * M);
-  for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < M + tw_len(M, E); i += blockDim.x) tw[i] = twg[i];
   const int t = threadIdx.x % P, ly = threadIdx.x / P;
   C* line = sm + ly * PITCH;
   const long ngroups = (nrows + TY - 1) / TY;
@@ -294,6 +296,7 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in
   };
   C nxt[E];
   load_group(blockIdx.x, nxt);
+  __syncthreads();  // twiddles
   for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const long row = grp * TY + ly;
     const bool ok = row < nrows;
@@ -301,12 +304,12 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_r2c(const T* __restrict__ in
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = nxt[m];
     load_group(grp + gridDim.x, nxt);
-    __syncthreads();  // twiddles; previous group's readers of `line` are done
-    line_fft<T, M, E, -1>(v, line, 1, t, tw, 2);
-    __syncthreads();
+    fft_bar<LB>();  // previous group's readers of `line` are done
+    line_fft<T, M, E, -1, LB>(v, line, 1, t, tw + M);
+    fft_bar<LB>();
 #pragma unroll
     for (int m = 0; m < E; ++m) line[xoff(t + P * m, 1)] = v[m];
-    __syncthreads();
+    fft_bar<LB>();
     if (ok) {
       C* dst = out + row * M;
 #pragma unroll
@@ -339,10 +342,11 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict_
   using C = cx<T>;
   constexpr int P = M / E;
   constexpr int PITCH = line_buf(M);
+  constexpr int LB = line_bar(P, 0);
   extern __shared__ __align__(16) unsigned char smraw[];
-  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);
+  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);  // as in k_x_r2c
   C* sm = reinterpret_cast<C*>(tw + 2 * M);
-  for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < M + tw_len(M, E); i += blockDim.x) tw[i] = twg[i];
   const int t = threadIdx.x % P, ly = threadIdx.x / P;
   C* line = sm + ly * PITCH;
   const KC<T> sc(scale);  // 1/(Nx Ny Nz), hi + lo in FP32
@@ -356,14 +360,15 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict_
   };
   C nxt[E];
   load_group(blockIdx.x, nxt);
+  __syncthreads();  // twiddles
   for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const long row = grp * TY + ly;
     const bool ok = row < nrows;
-    __syncthreads();  // twiddles; previous group's readers of `line` are done
+    fft_bar<LB>();  // previous group's readers of `line` are done
 #pragma unroll
     for (int m = 0; m < E; ++m) line[xoff(t + P * m, 1)] = nxt[m];
     load_group(grp + gridDim.x, nxt);
-    __syncthreads();
+    fft_bar<LB>();
     C v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -378,7 +383,7 @@ __global__ void __launch_bounds__((M / E) * TY) k_x_c2r(const cx<T>* __restrict_
         v[m] = C{s.x - wd.y, s.y + wd.x};  // s + i * wd
       }
     }
-    line_fft<T, M, E, +1>(v, line, 1, t, tw, 2);
+    line_fft<T, M, E, +1, LB>(v, line, 1, t, tw + M);
     if (ok) {
       T* dst = row < rows3 ? out_e + row * (2L * M) : out_h + (row - rows3) * (2L * M);
 #pragma unroll
@@ -402,9 +407,9 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
   using C = cx<T>;
   constexpr int P = N / E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);
+  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);  // stage-major table of (N, E)
   C* sm = reinterpret_cast<C*>(tw + N);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < tw_len(N, E); i += blockDim.x) tw[i] = twg[i];
   const int x = threadIdx.x % TX, t = threadIdx.x / TX;
   const long ntile_in = (inner + TX - 1) / TX;
   const long ntiles = ntile_in * outer;
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
     // in place: the next tile is another set of columns, never written by this tile
     load_tile(tile + gridDim.x, nxt);
     __syncthreads();  // twiddles
-    line_fft<T, N, E, DIR>(v, sm + x, TX, t, tw, 1);
+    line_fft<T, N, E, DIR>(v, sm + x, TX, t, tw);
     if (ok) {
 #pragma unroll
       for (int m = 0; m < E; ++m) base[(long)(t + P * m) * inner] = v[m];
@@ -455,9 +460,9 @@ __global__ void __launch_bounds__((N / E) * TX) k_z_fused(cx<T>* __restrict__ da
   using C = cx<T>;
   constexpr int P = N / E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);
+  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);  // stage-major table of (N, E)
   C* sm = reinterpret_cast<C*>(tw + N);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < tw_len(N, E); i += blockDim.x) tw[i] = twg[i];
   const int x = threadIdx.x % TX, t = threadIdx.x / TX;
   const long inner = (long)g.mx * g.ny;  // stride between z planes
   const long comp = inner * N;           // stride between components
@@ -481,7 +486,7 @@ __global__ void __launch_bounds__((N / E) * TX) k_z_fused(cx<T>* __restrict__ da
       for (int m = 0; m < E; ++m) v[c][m] = ok ? base[c * comp + (long)(t + P * m) * inner] : C{0, 0};
     __syncthreads();  // twiddles
 #pragma unroll
-    for (int c = 0; c < 6; ++c) line_fft<T, N, E, -1>(v[c], sm + x, TX + 1, t, tw, 1);
+    for (int c = 0; c < 6; ++c) line_fft<T, N, E, -1>(v[c], sm + x, TX + 1, t, tw);
     if (ok) {
       const int my = signed_index(y, g.ny);
       const T kx = nux * (T)col, ky = nuy * (T)my;
@@ -510,7 +515,7 @@ __global__ void __launch_bounds__((N / E) * TX) k_z_fused(cx<T>* __restrict__ da
       }
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) line_fft<T, N, E, +1>(v[c], sm + x, TX + 1, t, tw, 1);
+    for (int c = 0; c < 6; ++c) line_fft<T, N, E, +1>(v[c], sm + x, TX + 1, t, tw);
     if (ok) {
 #pragma unroll
       for (int c = 0; c < 6; ++c)

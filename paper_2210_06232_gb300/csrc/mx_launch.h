@@ -47,6 +47,10 @@ cudaError_t launch_gen_divfree(cx<T>* spec, long npts, const GridParams& g, unsi
 // of the literal form, in place on a spectrum after the x and y passes.
 // coef_kind as for launch_spectral (table kinds need `tab`, direct kinds ignore it).
 bool zfused_supported(int nz, bool fp64);
+// Values per thread of the line FFT plans: the FFT passes (length n) and the fused z pass
+// (0 when it has no plan for n); the twiddle tables are laid out for these plans.
+int fft_line_E(int n);
+int zfused_line_E(int n, bool fp64);
 template <typename T>
 cudaError_t launch_z_fused(int coef_kind, cx<T>* data, const GridParams& g, const void* tab, double t,
                            const twv<T>* tw, int grid, double* partials, unsigned* counter, double* record,

@@ -7,8 +7,8 @@
 // component) completing on an mbarrier, NST chunks in flight per block;
 // 256 threads consume a chunk (two points each) and write the result with
 // streaming 16-byte stores.  Waits on the mbarrier are bounded: a wait that
-// gives up sets counter[1] (read by the host as MX_E_TIMEOUT) and the block
-// leaves the loop at the next block-wide vote.
+// gives up sets counter[1] (read by the host as MX_E_TIMEOUT) and the warp
+// leaves the loop together.
 #pragma once
 #include "mx_kernels.cuh"
 
@@ -163,8 +163,10 @@ __global__ void __launch_bounds__(TMA_THREADS, 2)
       const bool live = p < npts;
       const int x0 = cur.x0, my = cur.my, mz = cur.mz;
       const float4 q4[2] = {cur.q[0], cur.q[1]};
-      if (!mbar_wait_bounded(&full[s], (i / TMA_NST) & 1u)) {
-        atomicExch(counter + 1, 1u);
+      // the warp leaves together (its lanes meet again in warp shuffles)
+      const bool lost = !mbar_wait_bounded(&full[s], (i / TMA_NST) & 1u);
+      if (__any_sync(0xffffffffu, lost)) {
+        if (lost) atomicExch(counter + 1, 1u);
         break;
       }
       const float4* st4 = reinterpret_cast<const float4*>(stage + (size_t)s * 6 * TMA_CH) + tid;

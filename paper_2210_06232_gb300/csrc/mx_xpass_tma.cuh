@@ -60,6 +60,7 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_r2c_tma(const T* __rest
   using C = cx<T>;
   constexpr int P = M / E;
   constexpr int NC = P * TY;
+  constexpr int LB = line_bar(P, NC);  // lines within a warp: __syncwarp; else named barrier over consumers
   constexpr size_t SB = xp_stage_bytes<T, M, TY>();
   extern __shared__ __align__(16) unsigned char smraw[];
   twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_r2c_tma(const T* __rest
   unsigned char* stages = reinterpret_cast<unsigned char*>(sm + TY * line_buf(M));
   uint64_t* full = reinterpret_cast<uint64_t*>(stages + XP_NST * SB);
   uint64_t* empty = full + XP_NST;
-  for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < M + tw_len(M, E); i += blockDim.x) tw[i] = twg[i];
   if (threadIdx.x == 0) {
     for (int s = 0; s < XP_NST; ++s) {
       mbar_init(&full[s], 1);
@@ -90,8 +91,10 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_r2c_tma(const T* __rest
     const int s = (int)(i % XP_NST);
     const long row = grp * TY + ly;
     const bool ok = row < nrows;
-    if (!mbar_wait_bounded(&full[s], (i / XP_NST) & 1u)) {
-      atomicExch(counter + 1, 1u);
+    // leave together: a thread that gave up waiting takes its barrier partners with it
+    const bool lost = !mbar_wait_bounded(&full[s], (i / XP_NST) & 1u);
+    if (fft_any<LB>(lost)) {
+      if (lost) atomicExch(counter + 1, 1u);
       break;
     }
     const C* st = reinterpret_cast<const C*>(stages + (size_t)s * SB) + (size_t)ly * M;
@@ -100,12 +103,11 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_r2c_tma(const T* __rest
     for (int m = 0; m < E; ++m) v[m] = ok ? st[t + P * m] : C{0, 0};
     fence_proxy_async_smem();
     mbar_arrive(&empty[s]);
-    line_fft<T, M, E, -1, NC>(v, line, 1, t, tw, 2);
-    // named barrier over the consumer threads only (the producer warp has left)
-    fft_bar<NC>();
+    line_fft<T, M, E, -1, LB>(v, line, 1, t, tw + M);
+    fft_bar<LB>();
 #pragma unroll
     for (int m = 0; m < E; ++m) line[xoff(t + P * m, 1)] = v[m];
-    fft_bar<NC>();
+    fft_bar<LB>();
     if (ok) {
       C* dst = out + row * M;
 #pragma unroll
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_r2c_tma(const T* __rest
         dst[k] = r;
       }
     }
-    fft_bar<NC>();  // `line` is reused by the next group
+    fft_bar<LB>();  // `line` is reused by the next group
   }
 }
 
@@ -137,6 +139,7 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_c2r_tma(const cx<T>* __
   using C = cx<T>;
   constexpr int P = M / E;
   constexpr int NC = P * TY;
+  constexpr int LB = line_bar(P, NC);  // lines within a warp: __syncwarp; else named barrier over consumers
   constexpr size_t SB = xp_stage_bytes<T, M, TY>();
   extern __shared__ __align__(16) unsigned char smraw[];
   twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_c2r_tma(const cx<T>* __
   unsigned char* stages = reinterpret_cast<unsigned char*>(sm + TY * line_buf(M));
   uint64_t* full = reinterpret_cast<uint64_t*>(stages + XP_NST * SB);
   uint64_t* empty = full + XP_NST;
-  for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < M + tw_len(M, E); i += blockDim.x) tw[i] = twg[i];
   if (threadIdx.x == 0) {
     for (int s = 0; s < XP_NST; ++s) {
       mbar_init(&full[s], 1);
@@ -169,8 +172,10 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_c2r_tma(const cx<T>* __
     const int s = (int)(i % XP_NST);
     const long row = grp * TY + ly;
     const bool ok = row < nrows;
-    if (!mbar_wait_bounded(&full[s], (i / XP_NST) & 1u)) {
-      atomicExch(counter + 1, 1u);
+    // leave together: a thread that gave up waiting takes its barrier partners with it
+    const bool lost = !mbar_wait_bounded(&full[s], (i / XP_NST) & 1u);
+    if (fft_any<LB>(lost)) {
+      if (lost) atomicExch(counter + 1, 1u);
       break;
     }
     const C* st = reinterpret_cast<const C*>(stages + (size_t)s * SB) + (size_t)ly * M;
@@ -190,8 +195,8 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_c2r_tma(const cx<T>* __
     }
     fence_proxy_async_smem();
     mbar_arrive(&empty[s]);
-    fft_bar<NC>();  // previous group's readers of `line` are done
-    line_fft<T, M, E, +1, NC>(v, line, 1, t, tw, 2);
+    fft_bar<LB>();  // previous group's readers of `line` are done
+    line_fft<T, M, E, +1, LB>(v, line, 1, t, tw + M);
     if (ok) {
       T* dst = row < rows3 ? out_e + row * (2L * M) : out_h + (row - rows3) * (2L * M);
 #pragma unroll

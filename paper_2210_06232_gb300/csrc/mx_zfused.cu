@@ -44,6 +44,8 @@ static cudaError_t zf_n(cx<T>* data, const GridParams& g, const void* tab, doubl
 }
 
 bool zfused_supported(int nz, bool fp64) { return fp64 ? zf_E<double>(nz) > 0 : zf_E<float>(nz) > 0; }
+int fft_line_E(int n) { return fft_E(n); }
+int zfused_line_E(int n, bool fp64) { return fp64 ? zf_E<double>(n) : zf_E<float>(n); }
 
 template <typename T, typename CoefT>
 static cudaError_t zf_dispatch(cx<T>* data, const GridParams& g, const void* tab, double t, const twv<T>* tw, int grid,

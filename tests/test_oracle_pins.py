@@ -304,3 +304,65 @@ def test_paper_energy_and_divergence_tables():
                 assert rel <= max(gold["example1_energy_drift"]["max_relative_drift_E1_to_E4"], 2e-15)
             assert r["divE_max"] <= max(gold["divergence"]["max_abs"], 1e-13)
             assert r["divH_max"] <= max(gold["divergence"]["max_abs"], 1e-13)
+
+
+# ------------------------------------------------------- symplecticity, convergence
+
+
+def _omega(E_a, H_a, E_b, H_b, eps, mu):
+    """Symplectic form of Thm 4.5 in the scaled variables u = sqrt(mu) H, v = sqrt(eps) E:
+    omega(a, b) = <v_a, u_b> - <u_a, v_b> (sum over all points and components)."""
+    ua, va = np.sqrt(mu) * H_a, np.sqrt(eps) * E_a
+    ub, vb = np.sqrt(mu) * H_b, np.sqrt(eps) * E_b
+    return float(np.sum(va * ub) - np.sum(ua * vb))
+
+
+def test_symplecticity_thm45():
+    """The step preserves dE ^ dH: omega(R a, R b) = omega(a, b) for two independent states."""
+    g = synth.Grid((8, 10, 6), (0, 0, 0), (1.0, 1.4, 0.9))
+    rng = np.random.default_rng(45)
+    Ea, Ha, Eb, Hb = (rng.standard_normal((3,) + g.shape) for _ in range(4))
+    eps, mu = 1.6, 0.7
+    w0 = _omega(Ea, Ha, Eb, Hb, eps, mu)
+    for t in (0.3, 4.0):
+        Ea1, Ha1 = scheme.solve(Ea, Ha, g.lo, g.hi, eps, mu, t)
+        Eb1, Hb1 = scheme.solve(Eb, Hb, g.lo, g.hi, eps, mu, t)
+        w1 = _omega(Ea1, Ha1, Eb1, Hb1, eps, mu)
+        assert abs(w1 - w0) < 1e-12 * (np.abs(Ea).sum() + np.abs(Eb).sum())
+    # and it is not trivially zero
+    assert abs(w0) > 1.0
+
+
+def test_spectral_convergence_thm34():
+    """Thm 3.4: for smooth, non-band-limited data the error decays faster than any power of N.
+
+    Initial fields E = curl A with A = (0, 0, exp(sin x) exp(cos y) cos z) (smooth, divergence
+    free, all wavenumbers present), H = 0; reference: the same scheme on a 48^3 grid, compared
+    at the coarse collocation points (which the fine grid contains since 48 is a multiple).
+    """
+    def fields(n):
+        g = synth.Grid((n, n, n))
+        x, y, z = g.mesh()
+        a = np.exp(np.sin(x)) * np.exp(np.cos(y))
+        # curl (0, 0, A_z) = (d_y A_z, -d_x A_z, 0)
+        Ex = a * (-np.sin(y)) * np.cos(z)
+        Ey = -(a * np.cos(x)) * np.cos(z)
+        E = np.stack([Ex, Ey, 0 * x])
+        return g, E, 0 * E
+
+    t = 0.7
+    gF, EF, HF = fields(48)
+    EfT, HfT = scheme.solve(EF, HF, gF.lo, gF.hi, 1.0, 1.0, t)
+    errs = []
+    for n in (8, 12, 16, 24):
+        g, E, H = fields(n)
+        Et, Ht = scheme.solve(E, H, g.lo, g.hi, 1.0, 1.0, t)
+        s = 48 // n
+        ref_E = EfT[:, ::s, ::s, ::s]
+        ref_H = HfT[:, ::s, ::s, ::s]
+        errs.append(np.sqrt(np.mean((Et - ref_E) ** 2) + np.mean((Ht - ref_H) ** 2)))
+    # faster than algebraic: each refinement gains more than the previous power law predicts
+    assert errs[-1] < 1e-6 * errs[0]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    rates = [np.log(errs[i] / errs[i + 1]) / np.log(n2 / n1) for i, (n1, n2) in enumerate([(8, 12), (12, 16), (16, 24)])]
+    assert rates[-1] > rates[0] > 2.0
