@@ -583,7 +583,7 @@ mx_status mx_create(mx_ctx** out, int nx, int ny, int nz, const double lo[3], co
   GridParams& g = c->g;
   g.nx = nx; g.ny = ny; g.nz = nz; g.mx = c->mx;
   grid_info(nx, ny, nz, lo, hi, g.nu, mmax);
-  g.eps = eps; g.mu = mu; g.c = 1.0 / sqrt(eps * mu);
+  mx::set_material(g, eps, mu);
   g.s0 = 0.0; g.qa[0] = g.qa[1] = g.qa[2] = 0;
   c->nq = 0;
   c->table = commensurate(g.nu, mmax, &g.s0, g.qa, &c->nq);

@@ -196,25 +196,30 @@ __host__ __device__ constexpr int tw_len(int N, int E) { return tw_stage_off(N, 
 //
 // v      : E registers, v[m] <-> position t + P*m
 // sm     : this line's exchange buffer, position p at sm[xoff(p, SS)]:
-//          p * SS for interleaved lines (SS > 1); for a contiguous line
-//          (SS == 1) one complex of padding every 16, which spreads the
-//          stride-R exchange writes over all banks.
+//          for interleaved lines (SS > 1, SS lines side by side) row p of SS
+//          values with one padding row every 8 rows, so that the rows written
+//          at stride R = 8 by neighbouring threads fall on different banks;
+//          for a contiguous line (SS == 1) one complex of padding every 16,
+//          which spreads the stride-R exchange writes over all banks.
 // tw     : stage-major twiddle table of (N, E) (tw_stage_off), twv<T> entries
 // All threads sharing the barrier must call this together (it synchronises):
 // NBAR < 0 uses __syncwarp() (each line within one warp), NBAR == 0
-// __syncthreads(), NBAR > 0 named barrier 1 over the first NBAR threads
+// __syncthreads(), NBAR > 0 the named barrier of this thread's group of NBAR
 // (warp-specialised kernels whose producer warp is busy).
-__device__ __forceinline__ int xoff(int p, int SS) { return SS == 1 ? p + (p >> 4) : p * SS; }
+__device__ __forceinline__ int xoff(int p, int SS) { return SS == 1 ? p + (p >> 4) : (p + (p >> 3)) * SS; }
 // Exchange-buffer length (complex values) of one contiguous line of length n.
 __host__ __device__ constexpr int line_buf(int n) { return n + (n >> 4) + 1; }
+// Rows of the exchange buffer of interleaved lines (SS > 1): one padding row every 8.
+__host__ __device__ constexpr int strided_rows(int n) { return n + (n >> 3) + 1; }
 
 // Barrier kinds: NBAR < 0 when every line lies within one warp (P threads per
-// line with P dividing 32): __syncwarp; 0: __syncthreads; > 0: named barrier 1
-// over the first NBAR threads.
+// line with P dividing 32): __syncwarp; 0: __syncthreads; > 0: named barrier
+// 1 + threadIdx.x / NBAR over NBAR threads (consecutive groups of NBAR threads
+// synchronise independently; barrier 0 stays __syncthreads).
 template <int NBAR> __device__ __forceinline__ void fft_bar() {
   if constexpr (NBAR < 0) __syncwarp();
   else if constexpr (NBAR == 0) __syncthreads();
-  else asm volatile("bar.sync 1, %0;" ::"r"(NBAR) : "memory");
+  else asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / NBAR), "r"(NBAR) : "memory");
 }
 // The same synchronisation, returning whether any participating thread had `v` set
 // (a uniform decision, e.g. to leave a loop together).
@@ -226,9 +231,9 @@ template <int NBAR> __device__ __forceinline__ bool fft_any(bool v) {
   } else {
     uint32_t r;
     asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %3, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
         : "=r"(r)
-        : "r"((uint32_t)v), "r"(NBAR)
+        : "r"((uint32_t)v), "r"(NBAR), "r"(1 + (int)threadIdx.x / NBAR)
         : "memory");
     return r != 0;
   }
@@ -236,24 +241,30 @@ template <int NBAR> __device__ __forceinline__ bool fft_any(bool v) {
 // Barrier kind for lines of P threads in blocks whose consumers synchronise with `wide`.
 __host__ __device__ constexpr int line_bar(int P, int wide) { return (P <= 32 && 32 % P == 0) ? -1 : wide; }
 
-template <typename T, int N, int E, int DIR, int NBAR = 0, int NS = 1>
-__device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, const twv<T>* tw) {
-  using C = cx<T>;
+// NL lines at once (v[l][m]; line l exchanges through sm + l * LS): the lines
+// share the barriers and each twiddle load, and their butterflies interleave.
+template <typename T, int N, int E, int DIR, int NBAR, int NL, int NS = 1>
+__device__ __forceinline__ void lines_fft(cx<T> (*v)[E], cx<T>* sm, int SS, int LS, int t, const twv<T>* tw) {
   if constexpr (NS < N) {
     constexpr int P = N / E;
     constexpr int R = pick_radix(N / NS, E);
     static_assert(R > 0, "no factorisation for this (N, E)");
-    constexpr int B = E / R;  // butterflies per thread
+    constexpr int B = E / R;  // butterflies per thread and line
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int j = t + P * b;
       const int k = j % NS;
       if constexpr (NS > 1) {
-#pragma unroll
         constexpr int OFF = tw_stage_off(N, E, NS);
-        for (int r = 1; r < R; ++r) v[b + r * B] = twmul<DIR>(v[b + r * B], tw[OFF + (r - 1) * NS + k]);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const twv<T> w = tw[OFF + (r - 1) * NS + k];
+#pragma unroll
+          for (int l = 0; l < NL; ++l) v[l][b + r * B] = twmul<DIR>(v[l][b + r * B], w);
+        }
       }
-      bfly<R, DIR, B>(v + b);
+#pragma unroll
+      for (int l = 0; l < NL; ++l) bfly<R, DIR, B>(v[l] + b);
     }
     if constexpr (NS * R < N) {
       fft_bar<NBAR>();  // previous readers of sm are done
@@ -263,14 +274,23 @@ __device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, con
         const int k = j % NS;
         const int base = (j / NS) * NS * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) sm[xoff(base + r * NS, SS)] = v[b + r * B];
+        for (int l = 0; l < NL; ++l)
+#pragma unroll
+          for (int r = 0; r < R; ++r) sm[l * LS + xoff(base + r * NS, SS)] = v[l][b + r * B];
       }
       fft_bar<NBAR>();
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = sm[xoff(t + P * m, SS)];
-      line_fft<T, N, E, DIR, NBAR, NS * R>(v, sm, SS, t, tw);
+      for (int l = 0; l < NL; ++l)
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[l][m] = sm[l * LS + xoff(t + P * m, SS)];
+      lines_fft<T, N, E, DIR, NBAR, NL, NS * R>(v, sm, SS, LS, t, tw);
     }
   }
+}
+
+template <typename T, int N, int E, int DIR, int NBAR = 0>
+__device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, const twv<T>* tw) {
+  lines_fft<T, N, E, DIR, NBAR, 1>(reinterpret_cast<cx<T>(*)[E]>(v), sm, SS, 0, t, tw);
 }
 
 }  // namespace mx

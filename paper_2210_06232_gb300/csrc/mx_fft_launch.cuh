@@ -22,9 +22,10 @@ constexpr int fft_TX(int n) { return clampi(256 / (n / fft_E(n)), 8, 64); }
   X(3) X(6) X(12) X(24) X(48) X(96) X(192) X(384) \
   X(5) X(10) X(20) X(40) X(80) X(160) X(320)
 
+// Dynamic shared memory of a launch; set every time (static shared memory of the
+// kernel adds to it, so the 48 KB default can be exceeded below 48 KB dynamic).
 template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 // Grid of a persistent FFT launch: `bps` blocks per SM (0 = one block per work item).
@@ -95,13 +96,13 @@ template <typename T, int N, int DIR>
 static cudaError_t strided_n(cx<T>* data, long inner, long outer, const twv<T>* tw, int bps, cudaStream_t s) {
   constexpr int E = fft_E(N), TX = fft_TX(N), P = N / E;
   static_assert(plan_ok(N, E), "plan");
-  const size_t smem = sizeof(twv<T>) * N + sizeof(cx<T>) * N * TX;
+  const size_t smem = sizeof(twv<T>) * N + sizeof(cx<T>) * strided_rows(N) * TX;
   auto k = k_fft_strided<T, N, E, TX, DIR>;
   cudaError_t err = set_smem(k, smem);
   if (err != cudaSuccess) return err;
   const long tiles = (inner + TX - 1) / TX * outer;
+  if (tiles > 0x7fffffffL) return cudaErrorInvalidConfiguration;  // the kernel counts tiles in 32 bits
   const long blocks = persistent_grid(tiles, bps);
-  if (blocks > 0x7fffffffL) return cudaErrorInvalidConfiguration;
   k<<<(unsigned)blocks, P * TX, smem, s>>>(data, inner, outer, tw);
   return cudaGetLastError();
 }

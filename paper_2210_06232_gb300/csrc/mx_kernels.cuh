@@ -18,6 +18,7 @@
 //                     many reals as the physical fields.
 #pragma once
 #include "mx_fft.cuh"
+#include "mx_tma.cuh"
 
 namespace mx {
 
@@ -29,7 +30,16 @@ struct GridParams {
   double s0;
   double eps, mu;
   double c;             // 1 / sqrt(eps mu)
+  double zh, ze;        // sqrt(eps / mu), sqrt(mu / eps)
 };
+// Material constants of a grid (host side).
+inline void set_material(GridParams& g, double eps, double mu) {
+  g.eps = eps;
+  g.mu = mu;
+  g.c = 1.0 / sqrt(eps * mu);
+  g.zh = sqrt(eps / mu);
+  g.ze = sqrt(mu / eps);
+}
 
 // Per-|k|^2 coefficients of the exact exponential (Prop. 2.1-2.2 rewritten
 // with k rather than k/|k|):
@@ -110,14 +120,23 @@ template <> struct Apply<float, CoefHL> {
 
 // Coefficients computed directly (no table): FP64 arithmetic per point.
 template <typename T, typename CoefT> __device__ __forceinline__ CoefT coef_direct(double k2, double t, const GridParams& g);
+// FP32 coefficients: the half phase th/2 = c |k| t / 2 is formed and reduced to
+// [-pi, pi] in FP64 (Cody-Waite reduction with 2 pi = hi + lo), so that large
+// c |k| t lose nothing; sin and cos of the reduced half angle are then taken in
+// FP32, which gives the FP32 coefficients to a few FP32 ulps:
+//   cos th = 1 - 2 sin^2(th/2), sin th = 2 sin(th/2) cos(th/2),
+//   (1 - cos th)/|k|^2 = 2 sin^2(th/2) / |k|^2.
 template <> __device__ __forceinline__ Coef<float> coef_direct<float, Coef<float>>(double k2, double t, const GridParams& g) {
   if (k2 == 0.0) return Coef<float>{1.f, 0.f, 0.f, 0.f};
-  double kabs = sqrt(k2), th = g.c * kabs * t, s, c;
-  sincos(th, &s, &c);
-  double sh;
-  sh = sin(0.5 * th);
-  double al = 2.0 * sh * sh / k2, b = s / kabs;
-  return Coef<float>{(float)c, (float)al, (float)(b * sqrt(g.eps / g.mu)), (float)(b * sqrt(g.mu / g.eps))};
+  const double kabs = sqrt(k2);
+  const double hp = 0.5 * g.c * kabs * t;
+  const double n = rint(hp * 0.15915494309189533577);  // 1 / (2 pi)
+  const double r = fma(-n, 2.4492935982947064e-16, fma(-n, 6.283185307179586, hp));
+  float sh, ch;
+  sincosf((float)r, &sh, &ch);
+  const float s = 2.f * sh * ch, sh2 = sh * sh;
+  const float b = s / (float)kabs;
+  return Coef<float>{1.f - 2.f * sh2, 2.f * sh2 / (float)k2, b * (float)g.zh, b * (float)g.ze};
 }
 template <> __device__ __forceinline__ Coef<double> coef_direct<double, Coef<double>>(double k2, double t, const GridParams& g) {
   if (k2 == 0.0) return Coef<double>{1.0, 0.0, 0.0, 0.0};
@@ -411,23 +430,27 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
   C* sm = reinterpret_cast<C*>(tw + N);
   for (int i = threadIdx.x; i < tw_len(N, E); i += blockDim.x) tw[i] = twg[i];
   const int x = threadIdx.x % TX, t = threadIdx.x / TX;
-  const long ntile_in = (inner + TX - 1) / TX;
-  const long ntiles = ntile_in * outer;
-  auto load_tile = [&](long tile, C* dst) {
-    const long o = tile / ntile_in;
-    const long col = (tile - o * ntile_in) * TX + x;
-    const bool ok = tile < ntiles && col < inner;
-    const C* b = data + o * N * inner + col;
+  // tile indices fit in 32 bits (checked by the launcher): 32-bit division per tile
+  const unsigned ntile_in = (unsigned)((inner + TX - 1) / TX);
+  const unsigned ntiles = ntile_in * (unsigned)outer;
+  const long pstride = (long)P * inner;  // between a thread's E positions
+  auto line_base = [&](unsigned tile, bool& ok) {
+    const unsigned o = tile / ntile_in;
+    const long col = (long)(tile - o * ntile_in) * TX + x;
+    ok = tile < ntiles && col < inner;
+    return data + (long)o * N * inner + col + (long)t * inner;
+  };
+  auto load_tile = [&](unsigned tile, C* dst) {
+    bool ok;
+    const C* b = line_base(tile, ok);
 #pragma unroll
-    for (int m = 0; m < E; ++m) dst[m] = ok ? b[(long)(t + P * m) * inner] : C{0, 0};
+    for (int m = 0; m < E; ++m) dst[m] = ok ? b[m * pstride] : C{0, 0};
   };
   C nxt[E];
   load_tile(blockIdx.x, nxt);
-  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long o = tile / ntile_in;
-    const long col = (tile - o * ntile_in) * TX + x;
-    const bool ok = col < inner;
-    C* base = data + o * N * inner + col;
+  for (unsigned tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    bool ok;
+    C* base = line_base(tile, ok);
     C v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = nxt[m];
@@ -437,7 +460,7 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
     line_fft<T, N, E, DIR>(v, sm + x, TX, t, tw);
     if (ok) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) base[(long)(t + P * m) * inner] = v[m];
+      for (int m = 0; m < E; ++m) base[m * pstride] = v[m];
     }
   }
 }
@@ -447,21 +470,62 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
 // For the literal form: the spectrum after the x and y passes is transformed
 // along z, multiplied by the exponential and transformed back, with all six
 // components of a tile (fixed ky, TX consecutive kx, every kz) held in
-// registers: thread (x, t) owns positions t + P*m of its column for the six
-// components, which are exactly the frequencies its forward transforms
-// produce and its inverse transforms consume (mx_fft.cuh).  One read and one
-// write of the spectrum replace three passes (z forward, update, z inverse).
-// Invariants of the updated state are summed as in the spectral pass.
-template <typename T, int N, int E, int TX, typename CoefT, bool INV>
-__global__ void __launch_bounds__((N / E) * TX) k_z_fused(cx<T>* __restrict__ data, GridParams g,
-                                                          const CoefT* __restrict__ tab, double tstep,
-                                                          const twv<T>* __restrict__ twg, double* __restrict__ partials,
-                                                          unsigned* __restrict__ counter, double* __restrict__ record) {
+// registers and transformed together (shared barriers and twiddle loads, one
+// exchange buffer per component): thread (x, t) owns positions t + P*m of its
+// column for the six components, which are exactly the frequencies its
+// forward transforms produce and its inverse transforms consume (mx_fft.cuh).
+// One read and one write of the spectrum replace three passes (z forward,
+// update, z inverse).  With TMAP the next tile is brought into a shared-memory
+// stage by the tensor copy engine while the current one is computed
+// (mx_zfused_tma.cuh supplies the loads).  Invariants of the updated state are
+// summed per thread in T over a tile, then per warp in a compensated (Kahan)
+// pair of T in shared memory, converted to FP64 at the end: no FP64 arithmetic
+// in the loop, where an FP64 instruction costs the pipe as much with one
+// active lane as with 32.
+template <typename T, int N, int E, int TX>
+struct ZTile {
+  static constexpr int P = N / E;
+  static constexpr int NZC = (N + 255) / 256;  // boxes of the tensor copy along z
+  static constexpr int ZC = N / NZC;           // z rows per box
+  static constexpr size_t stage_bytes = (size_t)6 * N * TX * sizeof(cx<T>);
+  static constexpr size_t exch_bytes = (size_t)6 * strided_rows(N) * TX * sizeof(cx<T>);
+  static constexpr size_t tw_bytes = (size_t)N * sizeof(twv<T>);
+  // static shared memory of the kernel: compensated sums and the block reduction
+  static constexpr size_t static_bytes = (size_t)2 * 32 * NSUM * sizeof(T) + (size_t)32 * NSUM * sizeof(double) + 128;
+  // element (comp c, z, column x) of the stage: box z / ZC, laid out [c][z % ZC][x]
+  __device__ __forceinline__ static int stage_index(int c, int z, int x) {
+    return (z / ZC) * (6 * ZC * TX) + (c * ZC + z % ZC) * TX + x;
+  }
+};
+
+// Thread 0: the tensor copies of tile `tile` into the stage, completing on `full`.
+template <typename T, int N, int E, int TX>
+__device__ __forceinline__ void z_tile_copy(const void* tmap, cx<T>* stage, uint64_t* full, long tile, int ntx) {
+  using ZT = ZTile<T, N, E, TX>;
+  const int y = (int)(tile / ntx);
+  const int x0 = (int)(tile - (long)y * ntx) * TX;
+  mbar_expect_tx(full, (uint32_t)ZT::stage_bytes);
+#pragma unroll
+  for (int h = 0; h < ZT::NZC; ++h)
+    tma_load_4d(reinterpret_cast<unsigned char*>(stage) + h * (ZT::stage_bytes / ZT::NZC), tmap, 2 * x0, y, h * ZT::ZC, 0,
+                full);
+}
+
+template <typename T, int N, int E, int TX, typename CoefT, bool INV, bool TMAP>
+__device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const GridParams& g, const CoefT* __restrict__ tab,
+                                             double tstep, const twv<T>* __restrict__ twg, double* __restrict__ partials,
+                                             unsigned* __restrict__ counter, double* __restrict__ record,
+                                             const void* tmap) {
   using C = cx<T>;
+  using ZT = ZTile<T, N, E, TX>;
   constexpr int P = N / E;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  twv<T>* tw = reinterpret_cast<twv<T>*>(smraw);  // stage-major table of (N, E)
-  C* sm = reinterpret_cast<C*>(tw + N);
+  constexpr int LS = strided_rows(N) * TX;  // exchange buffer of one component (TX lines side by side)
+  extern __shared__ __align__(128) unsigned char zsmraw[];
+  // [stage (TMAP only)][twiddles][exchange buffers][mbarrier]
+  C* stage = reinterpret_cast<C*>(zsmraw);
+  twv<T>* tw = reinterpret_cast<twv<T>*>(zsmraw + (TMAP ? ZT::stage_bytes : 0));
+  C* sm = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(tw) + ZT::tw_bytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(sm) + ZT::exch_bytes);
   for (int i = threadIdx.x; i < tw_len(N, E); i += blockDim.x) tw[i] = twg[i];
   const int x = threadIdx.x % TX, t = threadIdx.x / TX;
   const long inner = (long)g.mx * g.ny;  // stride between z planes
@@ -470,23 +534,54 @@ __global__ void __launch_bounds__((N / E) * TX) k_z_fused(cx<T>* __restrict__ da
   const long ntiles = (long)ntx * g.ny;
   const T eps = (T)g.eps, mu = (T)g.mu;
   const T nux = (T)g.nu[0], nuy = (T)g.nu[1], nuz = (T)g.nu[2];
-  double acc[INV ? NSUM : 1];
-  T part[INV ? NSUM : 1];
-#pragma unroll
-  for (int k = 0; k < (INV ? NSUM : 1); ++k) acc[k] = 0.0, part[k] = (T)0;
-  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  __shared__ T zhi[32][NSUM], zlo[32][NSUM];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (INV && lane == 0)
+    for (int k = 0; k < NSUM; ++k) zhi[warp][k] = zlo[warp][k] = (T)0;
+  if constexpr (TMAP) {
+    if (threadIdx.x == 0) {
+      mbar_init(full, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (long)blockIdx.x < ntiles) z_tile_copy<T, N, E, TX>(tmap, stage, full, blockIdx.x, ntx);
+  }
+  unsigned it = 0;
+  bool pending = (long)blockIdx.x < ntiles;  // a copy into the stage is in flight (thread 0's view)
+  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int y = (int)(tile / ntx);
     const int col = (int)(tile - (long)y * ntx) * TX + x;
     const bool ok = col < g.mx;
     C* base = data + (long)y * g.mx + col;
     C v[6][E];
+    if constexpr (TMAP) {
+      const bool lost = !mbar_wait_bounded(full, it & 1u);
+      if (__syncthreads_or(lost)) {
+        if (lost) atomicExch(counter + 1, 1u);
+        break;
+      }
 #pragma unroll
-    for (int c = 0; c < 6; ++c)
+      for (int c = 0; c < 6; ++c)
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[c][m] = ok ? base[c * comp + (long)(t + P * m) * inner] : C{0, 0};
-    __syncthreads();  // twiddles
+        for (int m = 0; m < E; ++m) v[c][m] = stage[ZT::stage_index(c, t + P * m, x)];
+      fence_proxy_async_smem();
+      __syncthreads();  // every read of the stage is done (and the twiddles are in)
+      pending = false;
+      if (threadIdx.x == 0 && tile + gridDim.x < ntiles) {
+        z_tile_copy<T, N, E, TX>(tmap, stage, full, tile + gridDim.x, ntx);
+        pending = true;
+      }
+    } else {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) line_fft<T, N, E, -1>(v[c], sm + x, TX + 1, t, tw);
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[c][m] = ok ? base[c * comp + (long)(t + P * m) * inner] : C{0, 0};
+      __syncthreads();  // twiddles
+    }
+    lines_fft<T, N, E, -1, 0, 6>(v, sm + x, TX, LS, t, tw);
+    T part[INV ? NSUM : 1];
+#pragma unroll
+    for (int k = 0; k < (INV ? NSUM : 1); ++k) part[k] = (T)0;
     if (ok) {
       const int my = signed_index(y, g.ny);
       const T kx = nux * (T)col, ky = nuy * (T)my;
@@ -509,21 +604,57 @@ __global__ void __launch_bounds__((N / E) * TX) k_z_fused(cx<T>* __restrict__ da
         for (int c = 0; c < 3; ++c) v[c][m] = ee[c], v[c + 3][m] = hh[c];
         if constexpr (INV) add_densities<T>(part, col == 0 ? (T)1 : (T)2, kx, ky, kz, hh, ee, eps, mu);
       }
-      if constexpr (INV) {
+    }
+    if constexpr (INV) {
 #pragma unroll
-        for (int k = 0; k < NSUM; ++k) acc[k] += (double)part[k], part[k] = (T)0;
+      for (int k = 0; k < NSUM; ++k) {
+        T w = part[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0) {  // hi + (-lo) carries the sum
+          const T yv = w - zlo[warp][k], tv = zhi[warp][k] + yv;
+          zlo[warp][k] = (tv - zhi[warp][k]) - yv;
+          zhi[warp][k] = tv;
+        }
       }
     }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) line_fft<T, N, E, +1>(v[c], sm + x, TX + 1, t, tw);
+    lines_fft<T, N, E, +1, 0, 6>(v, sm + x, TX, LS, t, tw);
     if (ok) {
+      // addresses recomputed here instead of kept live from the loads
+      C* sbase = base + (long)t * inner;
+      asm volatile("" : "+l"(sbase));
 #pragma unroll
       for (int c = 0; c < 6; ++c)
 #pragma unroll
-        for (int m = 0; m < E; ++m) base[c * comp + (long)(t + P * m) * inner] = v[c][m];
+        for (int m = 0; m < E; ++m) sbase[c * comp + (long)(P * m) * inner] = v[c][m];
     }
   }
-  if constexpr (INV) reduce_and_finish(acc, partials, counter, record);
+  if constexpr (TMAP) {
+    // after a timed-out wait: let the copy this block issued land before its shared memory is released
+    if (threadIdx.x == 0 && pending) mbar_wait_bounded(full, it & 1u);
+  }
+  if constexpr (INV) {
+    double acc[NSUM];
+#pragma unroll
+    for (int k = 0; k < NSUM; ++k) acc[k] = lane == 0 ? (double)zhi[warp][k] - (double)zlo[warp][k] : 0.0;
+    reduce_and_finish(acc, partials, counter, record);
+  }
+}
+
+template <typename T, int N, int E, int TX, typename CoefT, bool INV>
+__global__ void __launch_bounds__((N / E) * TX, 1)
+    k_z_fused_tma(cx<T>* __restrict__ data, GridParams g, const CoefT* __restrict__ tab, double tstep,
+                  const twv<T>* __restrict__ twg, double* __restrict__ partials, unsigned* __restrict__ counter,
+                  double* __restrict__ record, const __grid_constant__ CUtensorMap tmap) {
+  z_fused_body<T, N, E, TX, CoefT, INV, true>(data, g, tab, tstep, twg, partials, counter, record, &tmap);
+}
+
+template <typename T, int N, int E, int TX, typename CoefT, bool INV>
+__global__ void __launch_bounds__((N / E) * TX, 1) k_z_fused(cx<T>* __restrict__ data, GridParams g,
+                                                             const CoefT* __restrict__ tab, double tstep,
+                                                             const twv<T>* __restrict__ twg, double* __restrict__ partials,
+                                                             unsigned* __restrict__ counter, double* __restrict__ record) {
+  z_fused_body<T, N, E, TX, CoefT, INV, false>(data, g, tab, tstep, twg, partials, counter, record, nullptr);
 }
 
 // ------------------------------------------------------ spectral update pass

@@ -81,7 +81,7 @@ extern "C" mx_status mx_spectral_update_noalloc(const void* spec_in, void* spec_
   for (int w = 0; w < 3; ++w) g.nu[w] = 2.0 * M_PI / (hi[w] - lo[w]);
   g.qa[0] = g.qa[1] = g.qa[2] = 0;
   g.s0 = 0.0;
-  g.eps = eps; g.mu = mu; g.c = 1.0 / sqrt(eps * mu);
+  mx::set_material(g, eps, mu);
 
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* scratch = nullptr;

@@ -158,9 +158,7 @@ mx_status launch_request(Req* q) {
   // per-request eps and mu on a pooled context of the right grid and domain
   c->eps = q->r.eps;
   c->mu = q->r.mu;
-  c->g.eps = q->r.eps;
-  c->g.mu = q->r.mu;
-  c->g.c = 1.0 / sqrt(q->r.eps * q->r.mu);
+  mx::set_material(c->g, q->r.eps, q->r.mu);
   c->tab_t = NAN;  // coefficients depend on eps, mu and the domain
   mx_status st = mx_load_fields_async(c, q->r.E0, q->r.H0);
   if (st != MX_OK) return st;
