@@ -35,12 +35,12 @@ static long persistent_grid(long items, int bps) {
   return items < cap ? items : cap;
 }
 
-// Bulk-copy pipelined x passes: rows of at least 32 complex values, groups that
-// never straddle the E/H boundary, 16-byte aligned buffers.
+// Bulk-copy pipelined x passes: rows of at least 32 complex values, groups of
+// 2 TY rows that never straddle the E/H boundary, 16-byte aligned buffers.
 template <typename T, int M>
 static bool xp_tma_ok(const void* a, const void* b, long rows3) {
   constexpr int TY = fft_TY(M);
-  return M >= 32 && rows3 % TY == 0 && ((((uintptr_t)a) | ((uintptr_t)b)) & 15u) == 0;
+  return M >= 32 && rows3 % (2 * TY) == 0 && ((((uintptr_t)a) | ((uintptr_t)b)) & 15u) == 0;
 }
 
 template <typename T, int M>
@@ -54,7 +54,7 @@ static cudaError_t x_r2c_n(const T* e, const T* h, cx<T>* out, long rows3, long 
       auto k = k_x_r2c_tma<T, M, E, TY>;
       cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err != cudaSuccess) return err;
-      const long blocks = persistent_grid((nrows + TY - 1) / TY, bps > 0 ? bps : 2);
+      const long blocks = persistent_grid((nrows + 2 * TY - 1) / (2 * TY), bps > 0 ? bps : 2);
       k<<<(unsigned)blocks, P * TY + 32, smem, s>>>(e, h, out, rows3, nrows, tw, counter);
       return cudaGetLastError();
     }
@@ -78,7 +78,7 @@ static cudaError_t x_c2r_n(const cx<T>* in, T* e, T* h, long rows3, long nrows, 
       auto k = k_x_c2r_tma<T, M, E, TY>;
       cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err != cudaSuccess) return err;
-      const long blocks = persistent_grid((nrows + TY - 1) / TY, bps > 0 ? bps : 2);
+      const long blocks = persistent_grid((nrows + 2 * TY - 1) / (2 * TY), bps > 0 ? bps : 2);
       k<<<(unsigned)blocks, P * TY + 32, smem, s>>>(in, e, h, rows3, nrows, tw, scale, counter);
       return cudaGetLastError();
     }

@@ -502,8 +502,8 @@ struct ZTile {
 template <typename T, int N, int E, int TX>
 __device__ __forceinline__ void z_tile_copy(const void* tmap, cx<T>* stage, uint64_t* full, long tile, int ntx) {
   using ZT = ZTile<T, N, E, TX>;
-  const int y = (int)(tile / ntx);
-  const int x0 = (int)(tile - (long)y * ntx) * TX;
+  const int y = (int)((unsigned)tile / (unsigned)ntx);
+  const int x0 = (int)((unsigned)tile - (unsigned)y * (unsigned)ntx) * TX;
   mbar_expect_tx(full, (uint32_t)ZT::stage_bytes);
 #pragma unroll
   for (int h = 0; h < ZT::NZC; ++h)
@@ -549,8 +549,9 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
   unsigned it = 0;
   bool pending = (long)blockIdx.x < ntiles;  // a copy into the stage is in flight (thread 0's view)
   for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const int y = (int)(tile / ntx);
-    const int col = (int)(tile - (long)y * ntx) * TX + x;
+    // 32-bit division (a 64-bit one runs partly on the FP64 pipe); ntiles < 2^31
+    const int y = (int)((unsigned)tile / (unsigned)ntx);
+    const int col = (int)((unsigned)tile - (unsigned)y * (unsigned)ntx) * TX + x;
     const bool ok = col < g.mx;
     C* base = data + (long)y * g.mx + col;
     C v[6][E];
