@@ -47,6 +47,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Asynchronous global -> shared copies of 16-byte pieces (cp.async, L1 bypassed),
+// visible to the issuing thread after cp_async_wait_all().
+template <int BYTES>
+__device__ __forceinline__ void cp_async_16n(void* dst, const void* src) {
+  static_assert(BYTES % 16 == 0, "16-byte pieces");
+#pragma unroll
+  for (int o = 0; o < BYTES; o += 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32((const char*)dst + o)),
+                 "l"((const char*)src + o)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Tensor copy of one box of a 4D tensor map into shared memory, completing on
 // `bar` (coordinates in elements, innermost first; the box size is the map's).
 __device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2, int c3, uint64_t* bar) {

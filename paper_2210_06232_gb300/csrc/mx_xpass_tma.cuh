@@ -125,17 +125,41 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_r2c_tma(const T* __rest
     fence_proxy_async_smem();
     mbar_arrive(&L.empty[s]);
     lines_fft<T, M, E, -1, LB, 2>(v, line, 1, LS, t, tw + M);
-    fft_bar<LB>();
+    // Z_{M-k} of position k = t + P m: for t > 0 it is register E-1-m of thread P - t,
+    // for t = 0 register (E - m) mod E of this thread.  Lines within a warp fetch it
+    // with a shuffle, wider lines through the line buffer.
+    C zq[2][E];
+    if constexpr (LB < 0) {
+      const int lane = threadIdx.x & 31;
+      const int src = (lane & ~(P - 1)) | ((P - t) & (P - 1));
 #pragma unroll
-    for (int l = 0; l < 2; ++l)
+      for (int l = 0; l < 2; ++l)
 #pragma unroll
-      for (int m = 0; m < E; ++m) line[l * LS + xoff(t + P * m, 1)] = v[l][m];
-    fft_bar<LB>();
+        for (int m = 0; m < E; ++m) {
+          const C w = v[l][E - 1 - m];
+          const C sh = C{__shfl_sync(0xffffffffu, w.x, src), __shfl_sync(0xffffffffu, w.y, src)};
+          zq[l][m] = t == 0 ? v[l][(E - m) % E] : sh;
+        }
+    } else {
+      fft_bar<LB>();
+#pragma unroll
+      for (int l = 0; l < 2; ++l)
+#pragma unroll
+        for (int m = 0; m < E; ++m) line[l * LS + xoff(t + P * m, 1)] = v[l][m];
+      fft_bar<LB>();
+#pragma unroll
+      for (int l = 0; l < 2; ++l)
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const int k = t + P * m;
+          zq[l][m] = line[l * LS + xoff(k == 0 ? 0 : M - k, 1)];
+        }
+      fft_bar<LB>();  // the line buffers are reused by the next group
+    }
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
       const long row = grp * RY + ly + l * TY;
       if (row < nrows) {
-        const C* ln = line + l * LS;
         C* dst = out + row * M;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
@@ -145,7 +169,7 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_r2c_tma(const T* __rest
           if (k == 0) {
             r = C{z.x + z.y, z.x - z.y};
           } else {
-            C zp = cconj(ln[xoff(M - k, 1)]);
+            C zp = cconj(zq[l][m]);
             C a = cadd(z, zp), d = csub(z, zp);
             C b = C{d.y, -d.x};
             C wb = twmul<-1>(b, tw[k]);
@@ -155,7 +179,6 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_r2c_tma(const T* __rest
         }
       }
     }
-    fft_bar<LB>();  // the line buffers are reused by the next group
   }
 }
 
