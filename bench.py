@@ -176,18 +176,18 @@ def whole_job_value(world, units_per_rank, ms):
 KERNEL_NAMES = {
     "x_r2c": "k_x_r2c_tma (x-direction R2C, six fields)",
     "x_c2r": "k_x_c2r_tma (x-direction C2R, six fields)",
-    "y_fft": "k_fft_strided (y-direction, six components)",
+    "y_fft": "k_fft_strided (y-direction, six components; forward and inverse launches)",
     "z_fft": "k_fft_strided (z-direction, six components)",
-    "z_fused": "k_z_fused (z forward + exponential update + invariants + z inverse)",
+    "z_fused": "k_z_fused_tma (z forward + exponential update + invariants + z inverse, tensor-copy prefetch)",
     "spectral": "k_spectral_tma (exponential update + invariants)",
 }
 KERNEL_SOURCES = {
-    "x_r2c": ["mx_fft.cuh", "mx_kernels.cuh", "mx_xpass_tma.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
-    "x_c2r": ["mx_fft.cuh", "mx_kernels.cuh", "mx_xpass_tma.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
-    "y_fft": ["mx_fft.cuh", "mx_kernels.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
-    "z_fft": ["mx_fft.cuh", "mx_kernels.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
-    "z_fused": ["mx_fft.cuh", "mx_kernels.cuh", "mx_zfused.cu"],
-    "spectral": ["mx_fft.cuh", "mx_kernels.cuh", "mx_spectral_tma.cuh", "mx_spectral.cu"],
+    "x_r2c": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_xpass_tma.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
+    "x_c2r": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_xpass_tma.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
+    "y_fft": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
+    "z_fft": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
+    "z_fused": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_zfused.cu"],
+    "spectral": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_spectral_tma.cuh", "mx_spectral.cu"],
 }
 
 

@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_batch_steps(BatchArgs a) {
         T part[NSUM];
 #pragma unroll
         for (int k = 0; k < NSUM; ++k) part[k] = (T)0;
-        const T eps = (T)g.eps, mu = (T)g.mu;
+        const T eps = GP<T>::eps(g), mu = GP<T>::mu(g);
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
           const unsigned p = p0 + PPT * tid + j;
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_batch_steps(BatchArgs a) {
           const unsigned z = r / (unsigned)g.ny;
           const int y = (int)(r - z * (unsigned)g.ny);
           const int my = signed_index(y, g.ny), mz = signed_index((int)z, g.nz);
-          const T kx = (T)g.nu[0] * (T)x, ky = (T)g.nu[1] * (T)my, kz = (T)g.nu[2] * (T)mz;
+          const T kx = GP<T>::nu(g, 0) * (T)x, ky = GP<T>::nu(g, 1) * (T)my, kz = GP<T>::nu(g, 2) * (T)mz;
           Coef<T> q;
           if (b.tab) {
             // L1-bypassing load: the table was rewritten by other blocks in phase A

@@ -31,15 +31,31 @@ struct GridParams {
   double eps, mu;
   double c;             // 1 / sqrt(eps mu)
   double zh, ze;        // sqrt(eps / mu), sqrt(mu / eps)
+  float nuf[3], epsf, muf;  // FP32 copies for the FP32 kernels (no conversion on the FP64 pipe)
 };
-// Material constants of a grid (host side).
+// Material constants of a grid (host side; after nu is set).
 inline void set_material(GridParams& g, double eps, double mu) {
   g.eps = eps;
   g.mu = mu;
   g.c = 1.0 / sqrt(eps * mu);
   g.zh = sqrt(eps / mu);
   g.ze = sqrt(mu / eps);
+  for (int w = 0; w < 3; ++w) g.nuf[w] = (float)g.nu[w];
+  g.epsf = (float)eps;
+  g.muf = (float)mu;
 }
+// eps, mu and nu_w in the kernel's arithmetic type.
+template <typename T> struct GP;
+template <> struct GP<float> {
+  __device__ __forceinline__ static float eps(const GridParams& g) { return g.epsf; }
+  __device__ __forceinline__ static float mu(const GridParams& g) { return g.muf; }
+  __device__ __forceinline__ static float nu(const GridParams& g, int w) { return g.nuf[w]; }
+};
+template <> struct GP<double> {
+  __device__ __forceinline__ static double eps(const GridParams& g) { return g.eps; }
+  __device__ __forceinline__ static double mu(const GridParams& g) { return g.mu; }
+  __device__ __forceinline__ static double nu(const GridParams& g, int w) { return g.nu[w]; }
+};
 
 // Per-|k|^2 coefficients of the exact exponential (Prop. 2.1-2.2 rewritten
 // with k rather than k/|k|):
@@ -536,8 +552,8 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
   const long comp = inner * N;           // stride between components
   const int ntx = (g.mx + TX - 1) / TX;
   const long ntiles = (long)ntx * g.ny;
-  const T eps = (T)g.eps, mu = (T)g.mu;
-  const T nux = (T)g.nu[0], nuy = (T)g.nu[1], nuz = (T)g.nu[2];
+  const T eps = GP<T>::eps(g), mu = GP<T>::mu(g);
+  const T nux = GP<T>::nu(g, 0), nuy = GP<T>::nu(g, 1), nuz = GP<T>::nu(g, 2);
   __shared__ T zhi[32][NSUM], zlo[32][NSUM];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (INV && lane == 0)
@@ -719,8 +735,8 @@ __global__ void __launch_bounds__(256, 2) k_spectral(const cx<T>* __restrict__ s
   __shared__ double sacc[INV ? NSUM : 1][256];
   const unsigned npts = (unsigned)comp_stride;
   const unsigned mx = (unsigned)g.mx, ny = (unsigned)g.ny;
-  const T eps = (T)g.eps, mu = (T)g.mu;
-  const T nux = (T)g.nu[0], nuy = (T)g.nu[1], nuz = (T)g.nu[2];
+  const T eps = GP<T>::eps(g), mu = GP<T>::mu(g);
+  const T nux = GP<T>::nu(g, 0), nuy = GP<T>::nu(g, 1), nuz = GP<T>::nu(g, 2);
   T part[INV ? NSUM : 1];
   if constexpr (INV) {
 #pragma unroll

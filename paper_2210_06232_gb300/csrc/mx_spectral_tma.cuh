@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 2)
   } else {
     // ---------------------------------------------------------- consumers
     const unsigned mx = (unsigned)g.mx, ny = (unsigned)g.ny;
-    const float eps = (float)g.eps, mu = (float)g.mu;
-    const float nux = (float)g.nu[0], nuy = (float)g.nu[1], nuz = (float)g.nu[2];
+    const float eps = g.epsf, mu = g.muf;
+    const float nux = g.nuf[0], nuy = g.nuf[1], nuz = g.nuf[2];
     float part[INV ? NSUM : 1];
 #pragma unroll
     for (int k = 0; k < (INV ? NSUM : 1); ++k) part[k] = 0.f;
