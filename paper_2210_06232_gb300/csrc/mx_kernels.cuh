@@ -486,15 +486,14 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
 // For the literal form: the spectrum after the x and y passes is transformed
 // along z, multiplied by the exponential and transformed back, with all six
 // components of a tile (fixed ky, TX consecutive kx, every kz) held in
-// registers and transformed two at a time (shared barriers and twiddle loads,
-// one exchange buffer per component of a pair): thread (x, t) owns positions
-// t + P*m of its column for the six components, which are exactly the frequencies its
+// registers and transformed one after another through one exchange buffer:
+// thread (x, t) owns positions t + P*m of its column for the six components, which are exactly the frequencies its
 // forward transforms produce and its inverse transforms consume (mx_fft.cuh).
 // One read and one write of the spectrum replace three passes (z forward,
 // update, z inverse).  With TMAP the next tile is brought into a shared-memory
 // stage by the tensor copy engine while the current one is computed
-// The coefficient-table entries of a tile are copied to shared memory
-// (cp.async) while its forward transforms run.  Invariants of the updated state are
+// With TMAP the tile's results leave through an output stage and a tensor
+// store.  Invariants of the updated state are
 // summed per thread in T over a tile, then per warp in a compensated (Kahan)
 // pair of T in shared memory, converted to FP64 at the end: no FP64 arithmetic
 // in the loop, where an FP64 instruction costs the pipe as much with one
@@ -506,7 +505,7 @@ struct ZTile {
   static constexpr int ZC = N / NZC;           // z rows per box
   static constexpr size_t stage_bytes = (size_t)6 * N * TX * sizeof(cx<T>);
   static constexpr int NT = P * TX;  // threads
-  static constexpr int NL = 2;       // components transformed together (exchange buffers)
+  static constexpr int NL = 1;       // components transformed together (exchange buffers)
   static constexpr size_t exch_bytes = (size_t)NL * strided_rows(N) * TX * sizeof(cx<T>);
   static constexpr size_t tw_bytes = (size_t)N * sizeof(twv<T>);
   // static shared memory of the kernel: compensated sums and the block reduction
@@ -516,6 +515,19 @@ struct ZTile {
     return (z / ZC) * (6 * ZC * TX) + (c * ZC + z % ZC) * TX + x;
   }
 };
+
+// Thread 0: the tensor stores of tile `tile` from the output stage (one bulk group).
+template <typename T, int N, int E, int TX>
+__device__ __forceinline__ void z_tile_store(const void* tmap, const cx<T>* ostage, long tile, int ntx) {
+  using ZT = ZTile<T, N, E, TX>;
+  const int y = (int)((unsigned)tile / (unsigned)ntx);
+  const int x0 = (int)((unsigned)tile - (unsigned)y * (unsigned)ntx) * TX;
+#pragma unroll
+  for (int h = 0; h < ZT::NZC; ++h)
+    tma_store_4d(tmap, reinterpret_cast<const unsigned char*>(ostage) + h * (ZT::stage_bytes / ZT::NZC), 2 * x0, y,
+                 h * ZT::ZC, 0);
+  bulk_commit();
+}
 
 // Thread 0: the tensor copies of tile `tile` into the stage, completing on `full`.
 template <typename T, int N, int E, int TX>
@@ -540,12 +552,12 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
   constexpr int P = N / E;
   constexpr int LS = strided_rows(N) * TX;  // exchange buffer of one component (TX lines side by side)
   extern __shared__ __align__(128) unsigned char zsmraw[];
-  // [stage (TMAP only)][twiddles][exchange buffers][coefficients [E][NT]][mbarrier]
+  // [input stage, output stage (TMAP only)][twiddles][exchange buffer][mbarrier]
   C* stage = reinterpret_cast<C*>(zsmraw);
-  twv<T>* tw = reinterpret_cast<twv<T>*>(zsmraw + (TMAP ? ZT::stage_bytes : 0));
+  C* ostage = reinterpret_cast<C*>(zsmraw + ZT::stage_bytes);
+  twv<T>* tw = reinterpret_cast<twv<T>*>(zsmraw + (TMAP ? 2 * ZT::stage_bytes : 0));
   C* sm = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(tw) + ZT::tw_bytes);
-  CoefT* cst = reinterpret_cast<CoefT*>(reinterpret_cast<unsigned char*>(sm) + ZT::exch_bytes);
-  uint64_t* full = reinterpret_cast<uint64_t*>(cst + E * ZT::NT);
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(sm) + ZT::exch_bytes);
   for (int i = threadIdx.x; i < tw_len(N, E); i += blockDim.x) tw[i] = twg[i];
   const int x = threadIdx.x % TX, t = threadIdx.x / TX;
   const long inner = (long)g.mx * g.ny;  // stride between z planes
@@ -599,21 +611,9 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
         for (int m = 0; m < E; ++m) v[c][m] = ok ? base[c * comp + (long)(t + P * m) * inner] : C{0, 0};
       __syncthreads();  // twiddles
     }
-    // coefficient-table entries of this thread's points: copied to shared memory
-    // while the forward transforms run (their L2 latency is then off the update)
     const int my = signed_index(y, g.ny);
-    if (tab && ok) {
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const int mz = signed_index(t + P * m, N);
-        const CoefT* src = tab + (g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz);
-        cp_async_16n<sizeof(CoefT)>(cst + m * ZT::NT + threadIdx.x, src);
-      }
-      cp_async_commit();
-    }
 #pragma unroll
     for (int c = 0; c < 6; c += ZT::NL) lines_fft<T, N, E, -1, 0, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
-    if (tab && ok) cp_async_wait_all();
     T part[INV ? NSUM : 1];
 #pragma unroll
     for (int k = 0; k < (INV ? NSUM : 1); ++k) part[k] = (T)0;
@@ -625,7 +625,7 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
         const T kz = nuz * (T)mz;
         CoefT q;
         if (tab) {
-          q = cst[m * ZT::NT + threadIdx.x];
+          q = tab[g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz];
         } else {
           const double k2 = g.nu[0] * g.nu[0] * (double)col * col + g.nu[1] * g.nu[1] * (double)my * my +
                             g.nu[2] * g.nu[2] * (double)mz * mz;
@@ -654,7 +654,18 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
     }
 #pragma unroll
     for (int c = 0; c < 6; c += ZT::NL) lines_fft<T, N, E, +1, 0, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
-    if (ok) {
+    if constexpr (TMAP) {
+      // through the output stage and the tensor-copy engine (it drops the columns past Mx)
+      if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tile's store has read the stage
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) ostage[ZT::stage_index(c, t + P * m, x)] = v[c][m];
+      fence_proxy_async_smem();  // generic writes before the async-proxy reads of the store
+      __syncthreads();
+      if (threadIdx.x == 0) z_tile_store<T, N, E, TX>(tmap, ostage, tile, ntx);
+    } else if (ok) {
       // addresses recomputed here instead of kept live from the loads
       C* sbase = base + (long)t * inner;
       asm volatile("" : "+l"(sbase));
@@ -667,6 +678,7 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
   if constexpr (TMAP) {
     // after a timed-out wait: let the copy this block issued land before its shared memory is released
     if (threadIdx.x == 0 && pending) mbar_wait_bounded(full, it & 1u);
+    if (threadIdx.x == 0) bulk_wait_all();  // the last stores have completed
   }
   if constexpr (INV) {
     double acc[NSUM];

@@ -68,8 +68,7 @@ static cudaError_t zf_n(cx<T>* data, const GridParams& g, const void* tab, doubl
     const CoefT* tb = reinterpret_cast<const CoefT*>(tab);
     cudaError_t err;
     // with the tensor-copy prefetch when the stage fits beside the exchange buffers
-    constexpr size_t coef_bytes = (size_t)E * ZT::NT * sizeof(CoefT);
-    constexpr size_t smem_tma = ZT::stage_bytes + ZT::tw_bytes + ZT::exch_bytes + coef_bytes + 16;
+    constexpr size_t smem_tma = 2 * ZT::stage_bytes + ZT::tw_bytes + ZT::exch_bytes + 16;
     if constexpr (smem_tma + ZT::static_bytes <= 232448) {  // shared memory of a block on sm_103a
       CUtensorMap m;
       if (counter && z_tensor_map<T, N, E, TX>(&m, data, g)) {
@@ -85,7 +84,7 @@ static cudaError_t zf_n(cx<T>* data, const GridParams& g, const void* tab, doubl
         return cudaGetLastError();
       }
     }
-    const size_t smem = ZT::tw_bytes + ZT::exch_bytes + coef_bytes + 16;
+    const size_t smem = ZT::tw_bytes + ZT::exch_bytes + 16;
     if (record) {
       auto k = k_z_fused<T, N, E, TX, CoefT, true>;
       if ((err = set_smem(k, smem)) != cudaSuccess) return err;
