@@ -262,12 +262,12 @@ cudaError_t forward3(mx_ctx* c, const T* e, const T* h, void* spec, bool with_z 
   {
     ProfScope ps(c, MX_K_Y_FFT);
     err = mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, pass_bps(c, P_Y_FWD),
-                                c->stream);
+                                c->stream, c->counter);
   }
   if (err != cudaSuccess || !with_z) return err;
   ProfScope ps(c, MX_K_Z_FFT);
   return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, pass_bps(c, P_Z_FWD),
-                               c->stream);
+                               c->stream, c->counter);
 }
 
 template <typename T>
@@ -278,13 +278,13 @@ cudaError_t inverse3(mx_ctx* c, void* spec, T* e, T* h, bool with_z = true) {
   if (with_z) {
     ProfScope ps(c, MX_K_Z_FFT);
     err = mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, pass_bps(c, P_Z_INV),
-                                c->stream);
+                                c->stream, c->counter);
   }
   if (err != cudaSuccess) return err;
   {
     ProfScope ps(c, MX_K_Y_FFT);
     err = mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, pass_bps(c, P_Y_INV),
-                                c->stream);
+                                c->stream, c->counter);
   }
   if (err != cudaSuccess) return err;
   const double scale = 1.0 / (double)c->ns;
@@ -304,12 +304,12 @@ cudaError_t run_pass(mx_ctx* c, int pass, int bps) {
   switch (pass) {
     case P_X_R2C:
       return mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, bps, c->stream, c->counter);
-    case P_Y_FWD: return mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream);
+    case P_Y_FWD: return mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream, c->counter);
     case P_Z_FWD:
-      return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream);
+      return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream, c->counter);
     case P_Z_INV:
-      return mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream);
-    case P_Y_INV: return mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream);
+      return mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream, c->counter);
+    case P_Y_INV: return mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream, c->counter);
     case P_X_C2R:
       return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, 1.0, bps, c->stream,
                                  c->counter);

@@ -2,6 +2,8 @@
 // mx_fft_f32.cu and mx_fft_f64.cu.
 #pragma once
 #include "mx_launch.h"
+#include "mx_strided_tma.cuh"
+#include "mx_tmap.h"
 #include "mx_xpass_tma.cuh"
 
 namespace mx {
@@ -93,15 +95,31 @@ static cudaError_t x_c2r_n(const cx<T>* in, T* e, T* h, long rows3, long nrows, 
 }
 
 template <typename T, int N, int DIR>
-static cudaError_t strided_n(cx<T>* data, long inner, long outer, const twv<T>* tw, int bps, cudaStream_t s) {
+static cudaError_t strided_n(cx<T>* data, long inner, long outer, const twv<T>* tw, int bps, cudaStream_t s,
+                             unsigned* counter) {
   constexpr int E = fft_E(N), TX = fft_TX(N), P = N / E;
   static_assert(plan_ok(N, E), "plan");
+  const long tiles = (inner + TX - 1) / TX * outer;
+  if (tiles > 0x7fffffffL) return cudaErrorInvalidConfiguration;  // the kernels count tiles in 32 bits
+  using ST = STile<T, N, E, TX>;
+  if constexpr (ST::smem <= 232448) {  // shared memory of a block on sm_103a
+    // tensor-copy loads and stores of [outer][N][inner] complex as scalars
+    CUtensorMap m;
+    const cuuint64_t dim[3] = {(cuuint64_t)(2 * inner), (cuuint64_t)N, (cuuint64_t)outer};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * TX), (cuuint32_t)ST::ZC, 1};
+    if (counter && tensor_map(&m, (int)sizeof(T), 3, data, dim, box)) {
+      auto k = k_fft_strided_tma<T, N, E, TX, DIR>;
+      cudaError_t err = set_smem(k, ST::smem);
+      if (err != cudaSuccess) return err;
+      const long blocks = persistent_grid(tiles, bps > 0 ? bps : 1);
+      k<<<(unsigned)blocks, P * TX, ST::smem, s>>>(inner, outer, tw, counter, m);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = sizeof(twv<T>) * N + sizeof(cx<T>) * strided_rows(N) * TX;
   auto k = k_fft_strided<T, N, E, TX, DIR>;
   cudaError_t err = set_smem(k, smem);
   if (err != cudaSuccess) return err;
-  const long tiles = (inner + TX - 1) / TX * outer;
-  if (tiles > 0x7fffffffL) return cudaErrorInvalidConfiguration;  // the kernel counts tiles in 32 bits
   const long blocks = persistent_grid(tiles, bps);
   k<<<(unsigned)blocks, P * TX, smem, s>>>(data, inner, outer, tw);
   return cudaGetLastError();
@@ -133,17 +151,17 @@ cudaError_t launch_x_c2r(int M, const cx<T>* in, T* e, T* h, long rows3, long nr
 
 template <typename T>
 cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const twv<T>* tw, int bps,
-                           cudaStream_t s) {
+                           cudaStream_t s, unsigned* counter) {
   if (inner <= 0 || outer <= 0 || N == 1) return cudaSuccess;
   if (dir < 0) {
     switch (N) {
-#define X(n) case n: return strided_n<T, n, -1>(data, inner, outer, tw, bps, s);
+#define X(n) case n: return strided_n<T, n, -1>(data, inner, outer, tw, bps, s, counter);
       MX_FOR_EACH_LEN(X)
 #undef X
     }
   } else {
     switch (N) {
-#define X(n) case n: return strided_n<T, n, +1>(data, inner, outer, tw, bps, s);
+#define X(n) case n: return strided_n<T, n, +1>(data, inner, outer, tw, bps, s, counter);
       MX_FOR_EACH_LEN(X)
 #undef X
     }

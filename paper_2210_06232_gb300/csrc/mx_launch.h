@@ -26,7 +26,7 @@ cudaError_t launch_x_c2r(int M, const cx<T>* in, T* out_e, T* out_h, long rows3,
 // dir = -1 forward, +1 inverse (unnormalised)
 template <typename T>
 cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const twv<T>* tw, int bps,
-                           cudaStream_t s);
+                           cudaStream_t s, unsigned* counter = nullptr);
 
 // Spectral pass.  mode: 0 = invariants only, 1 = update only, 2 = update + invariants.
 // coef_kind: 0 = Coef<T> table, 1 = CoefHL table (float only), 2 = direct Coef<T>, 3 = direct CoefHL.

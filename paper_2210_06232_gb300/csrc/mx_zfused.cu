@@ -1,6 +1,4 @@
 // Launchers of the fused z pass of the literal form (see k_z_fused).
-#include <cudaTypedefs.h>
-
 #include "mx_fft_launch.cuh"
 
 namespace mx {
@@ -19,39 +17,13 @@ template <typename T> constexpr int zf_TX(int n) {
 
 #define MX_ZF_LENS(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(6) X(12) X(24) X(48) X(96) X(192) X(384)
 
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
-static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      (void)cudaGetLastError();
-  }
-  return fn;
-}
-
 // Tensor map of the spectrum as [6][nz][ny][2 Mx] scalars, box [6][ZC][1][2 TX].
 template <typename T, int N, int E, int TX>
 static bool z_tensor_map(CUtensorMap* m, const void* data, const GridParams& g) {
   using ZT = ZTile<T, N, E, TX>;
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
-  if (!enc) return false;
-  const cuuint64_t es = sizeof(T);
   const cuuint64_t dim[4] = {(cuuint64_t)2 * g.mx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 6};
-  const cuuint64_t stride[3] = {dim[0] * es, dim[0] * dim[1] * es, dim[0] * dim[1] * dim[2] * es};
   const cuuint32_t box[4] = {(cuuint32_t)(2 * TX), 1, (cuuint32_t)ZT::ZC, 6};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  if ((((uintptr_t)data) & 15u) || (stride[0] & 15u)) return false;
-  const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-  return enc(m, dt, 4, const_cast<void*>(data), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
+  return tensor_map(m, (int)sizeof(T), 4, data, dim, box);
 }
 
 template <typename T, int N, typename CoefT>
