@@ -176,7 +176,7 @@ def whole_job_value(world, units_per_rank, ms):
 KERNEL_NAMES = {
     "x_r2c": "k_x_r2c_tma (x-direction R2C, six fields)",
     "x_c2r": "k_x_c2r_tma (x-direction C2R, six fields)",
-    "y_fft": "k_fft_strided (y-direction, six components; forward and inverse launches)",
+    "y_fft": "k_fft_strided_tma (y-direction, six components; forward and inverse launches)",
     "z_fft": "k_fft_strided (z-direction, six components)",
     "z_fused": "k_z_fused_tma (z forward + exponential update + invariants + z inverse, tensor-copy prefetch)",
     "spectral": "k_spectral_tma (exponential update + invariants)",
@@ -184,9 +184,11 @@ KERNEL_NAMES = {
 KERNEL_SOURCES = {
     "x_r2c": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_xpass_tma.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
     "x_c2r": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_xpass_tma.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
-    "y_fft": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
-    "z_fft": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
-    "z_fused": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_zfused.cu"],
+    "y_fft": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_strided_tma.cuh", "mx_tmap.h", "mx_fft_launch.cuh",
+              "mx_fft_f32.cu"],
+    "z_fft": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_strided_tma.cuh", "mx_tmap.h", "mx_fft_launch.cuh",
+              "mx_fft_f32.cu"],
+    "z_fused": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_tmap.h", "mx_zfused.cu"],
     "spectral": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_spectral_tma.cuh", "mx_spectral.cu"],
 }
 
