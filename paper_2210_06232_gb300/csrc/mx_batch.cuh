@@ -131,6 +131,21 @@ __device__ __forceinline__ Coef<double> load_coef_cg(const Coef<double>* p) {
 }
 
 __device__ __forceinline__ bool recorded(const BInst& b, long long N) { return b.every > 0 && N % b.every == 0; }
+
+// Instance of global chunk `key`: binary search over the first chunks held in shared
+// memory (batches of up to BT_SINST instances), else over the descriptors.
+constexpr int BT_SINST = 1024;
+static_assert(BTraits<float>::PPT <= 2 && BTraits<double>::PPT <= 2, "a thread's points cross at most one row end");
+__device__ __forceinline__ int find_inst_s(const BatchArgs& a, const unsigned* s_chunk0, unsigned key) {
+  if (a.ninst > BT_SINST) return find_inst(a.inst, a.ninst, key, true);
+  int lo = 0, hi = a.ninst - 1;
+  while (lo < hi) {  // last instance whose first chunk <= key
+    const int mid = (lo + hi + 1) >> 1;
+    if (s_chunk0[mid] <= key) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 __device__ __forceinline__ long long rec_slot(const BInst& b, long long N) { return N / b.every - b.n0 / b.every - 1; }
 
 // Transpose reduction of 16 values across a warp (value 15 is padding): after
@@ -240,7 +255,7 @@ __device__ void batch_final(const BatchArgs& a, long long step_local, const doub
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BT_THREADS, 2) k_batch_steps(BatchArgs a) {
+__global__ void __maxnreg__(112) k_batch_steps(BatchArgs a) {  // 2 blocks of BT_THREADS per SM
   using C = cx<T>;
   constexpr int PPT = BTraits<T>::PPT;
   constexpr int CH = bt_ch<T>();
@@ -249,6 +264,8 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_batch_steps(BatchArgs a) {
   uint64_t* full = reinterpret_cast<uint64_t*>(smraw + (size_t)BT_NST * 6 * CH * sizeof(C));
   uint64_t* empty = full + BT_NST;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ unsigned s_chunk0[BT_SINST];  // first chunk of each instance (instance lookup)
+  for (int k = tid; k < a.ninst && k < BT_SINST; k += blockDim.x) s_chunk0[k] = a.inst[k].chunk0;
   if (tid == 0) {
     for (int s = 0; s < BT_NST; ++s) {
       mbar_init(&full[s], 1);
@@ -290,7 +307,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_batch_steps(BatchArgs a) {
             ok = false;
             break;
           }
-          const BInst& b = a.inst[find_inst(a.inst, a.ninst, gc, true)];
+          const BInst& b = a.inst[find_inst_s(a, s_chunk0, gc)];
           const unsigned p0 = (gc - b.chunk0) * CH;
           const unsigned cnt = min((unsigned)CH, b.npts - p0);
           const uint32_t bytes = cnt * (uint32_t)sizeof(C);
@@ -307,14 +324,64 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_batch_steps(BatchArgs a) {
         }
       }
     } else {
-      unsigned ii = i;
-      for (unsigned gc = blockIdx.x; gc < a.total_chunks; gc += gridDim.x, ++ii) {
-        const int s = (int)(ii % BT_NST);
-        const BInst& b = a.inst[find_inst(a.inst, a.ninst, gc, true)];
+      // Everything a chunk needs besides its data (instance, wavenumbers, coefficients) is
+      // prepared one chunk ahead, so the coefficient loads from L2 overlap the current chunk.
+      struct Pt {
+        Coef<T> q;
+        T kx, ky, kz, w;  // w: Hermitian weight, 0 past the instance's last point
+      };
+      struct Prep {
+        int ii;
+        unsigned p0;
+        bool rec;
+        Pt pt[PPT];
+      };
+      auto prep = [&](unsigned gc, Prep& o) {
+        o.ii = find_inst_s(a, s_chunk0, gc);
+        const BInst& b = a.inst[o.ii];
         const GridParams& g = b.g;
-        const unsigned p0 = (gc - b.chunk0) * CH;
-        const long long N = b.n0 + n;
-        const bool rec = recorded(b, N);
+        o.p0 = (gc - b.chunk0) * CH;
+        o.rec = recorded(b, b.n0 + n);
+        // row of this thread's first point; the next one is in it or starts the next row
+        const unsigned pf = o.p0 + PPT * tid;
+        const unsigned rf = (pf < b.npts ? pf : 0u) / (unsigned)g.mx;
+        const int xf = (int)((pf < b.npts ? pf : 0u) - rf * (unsigned)g.mx);
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+          const unsigned p = pf + j;
+          const bool live = p < b.npts;
+          const bool wrap = xf + j >= g.mx;  // PPT <= 2 crosses at most one row end
+          const unsigned r = live ? rf + (wrap ? 1u : 0u) : 0u;
+          const int x = live ? xf + j - (wrap ? g.mx : 0) : 0;
+          const unsigned z = r / (unsigned)g.ny;
+          const int y = (int)(r - z * (unsigned)g.ny);
+          const int my = signed_index(y, g.ny), mz = signed_index((int)z, g.nz);
+          Pt& q = o.pt[j];
+          q.kx = GP<T>::nu(g, 0) * (T)x;
+          q.ky = GP<T>::nu(g, 1) * (T)my;
+          q.kz = GP<T>::nu(g, 2) * (T)mz;
+          q.w = live ? (x == 0 ? (T)1 : (T)2) : (T)0;
+          if (b.tab) {
+            // L1-bypassing load: the table was rewritten by other blocks in phase A
+            q.q = load_coef_cg(reinterpret_cast<const Coef<T>*>(b.tab) + (g.qa[0] * x * x + g.qa[1] * my * my +
+                                                                          g.qa[2] * mz * mz));
+          } else {
+            const double k2 = g.nu[0] * g.nu[0] * (double)x * x + g.nu[1] * g.nu[1] * (double)my * my +
+                              g.nu[2] * g.nu[2] * (double)mz * mz;
+            q.q = coef_direct<T, Coef<T>>(k2, b.t0 + (double)n * b.h, g);
+          }
+        }
+      };
+      unsigned ii = i;
+      Prep cur, nxt;
+      if (blockIdx.x < a.total_chunks) prep(blockIdx.x, cur);
+      for (unsigned gc = blockIdx.x; gc < a.total_chunks; gc += gridDim.x, ++ii, cur = nxt) {
+        const int s = (int)(ii % BT_NST);
+        if (gc + gridDim.x < a.total_chunks) prep(gc + gridDim.x, nxt);
+        const BInst& b = a.inst[cur.ii];
+        const GridParams& g = b.g;
+        const unsigned p0 = cur.p0;
+        const bool rec = cur.rec;
         // the warp leaves together (its lanes meet again in warp shuffles)
         const bool lost = !mbar_wait_bounded(&full[s], (ii / BT_NST) & 1u);
         if (__any_sync(0xffffffffu, lost)) {
@@ -335,30 +402,14 @@ __global__ void __launch_bounds__(BT_THREADS, 2) k_batch_steps(BatchArgs a) {
         const T eps = GP<T>::eps(g), mu = GP<T>::mu(g);
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
-          const unsigned p = p0 + PPT * tid + j;
-          if (p >= b.npts) continue;
-          const unsigned r = p / (unsigned)g.mx;
-          const int x = (int)(p - r * (unsigned)g.mx);
-          const unsigned z = r / (unsigned)g.ny;
-          const int y = (int)(r - z * (unsigned)g.ny);
-          const int my = signed_index(y, g.ny), mz = signed_index((int)z, g.nz);
-          const T kx = GP<T>::nu(g, 0) * (T)x, ky = GP<T>::nu(g, 1) * (T)my, kz = GP<T>::nu(g, 2) * (T)mz;
-          Coef<T> q;
-          if (b.tab) {
-            // L1-bypassing load: the table was rewritten by other blocks in phase A
-            q = load_coef_cg(reinterpret_cast<const Coef<T>*>(b.tab) + (g.qa[0] * x * x + g.qa[1] * my * my +
-                                                                        g.qa[2] * mz * mz));
-          } else {
-            const double k2 = g.nu[0] * g.nu[0] * (double)x * x + g.nu[1] * g.nu[1] * (double)my * my +
-                              g.nu[2] * g.nu[2] * (double)mz * mz;
-            q = coef_direct<T, Coef<T>>(k2, b.t0 + (double)n * b.h, g);
-          }
+          const Pt& q = cur.pt[j];
+          if (q.w == (T)0) continue;
           C hh[3] = {v[3][j], v[4][j], v[5][j]};
           C ee[3] = {v[0][j], v[1][j], v[2][j]};
-          Apply<T, Coef<T>>::run(q, kx, ky, kz, hh, ee);
+          Apply<T, Coef<T>>::run(q.q, q.kx, q.ky, q.kz, hh, ee);
 #pragma unroll
           for (int comp = 0; comp < 3; ++comp) v[comp][j] = ee[comp], v[comp + 3][j] = hh[comp];
-          if (rec) add_densities<T>(part, x == 0 ? (T)1 : (T)2, kx, ky, kz, hh, ee, eps, mu);
+          if (rec) add_densities<T>(part, q.w, q.kx, q.ky, q.kz, hh, ee, eps, mu);
         }
         C* dst = reinterpret_cast<C*>(b.dst);
         const unsigned pt = p0 + PPT * tid;
