@@ -216,3 +216,28 @@ def test_errors_are_status_codes():
     s.close()
     assert mx.mx_create(C.byref(h), 14, 8, 8, lo, hi, 1.0, 1.0, 0, 0, None) == mx.MX_E_UNSUPPORTED_N
     assert not h.value
+
+
+def _omega(Ea, Ha, Eb, Hb, eps, mu):
+    """Symplectic form of Thm 4.5 in u = sqrt(mu) H, v = sqrt(eps) E: <v_a, u_b> - <u_a, v_b>."""
+    return float(np.sum(np.sqrt(eps) * Ea * np.sqrt(mu) * Hb) - np.sum(np.sqrt(mu) * Ha * np.sqrt(eps) * Eb))
+
+
+@pytest.mark.parametrize("form", ["literal", "spectral"])
+def test_symplectic_form_preserved_fp64(form):
+    """Thm 4.5 on the GPU: the step preserves dE ^ dH, omega(R a, R b) = omega(a, b), for two
+    independent states (not divergence free, every wavenumber populated)."""
+    mx = _mx()
+    g = synth.Grid((12, 10, 8), (0, 0, 0), (1.0, 1.4, 0.9))
+    rng = np.random.default_rng(45)
+    Ea, Ha, Eb, Hb = (rng.standard_normal((3,) + g.shape) for _ in range(4))
+    eps, mu = 1.6, 0.7
+    F = mx.MX_FORM_LITERAL if form == "literal" else mx.MX_FORM_SPECTRAL
+    Ea1, Ha1, _ = run_gpu(g, Ea, Ha, eps, mu, mx.MX_FP64, F, 0.3, 10, every=0)
+    Eb1, Hb1, _ = run_gpu(g, Eb, Hb, eps, mu, mx.MX_FP64, F, 0.3, 10, every=0)
+    w0 = _omega(Ea, Ha, Eb, Hb, eps, mu)
+    w1 = _omega(Ea1, Ha1, Eb1, Hb1, eps, mu)
+    na = np.sqrt(eps * np.sum(Ea ** 2) + mu * np.sum(Ha ** 2))
+    nb = np.sqrt(eps * np.sum(Eb ** 2) + mu * np.sum(Hb ** 2))
+    assert abs(w0) > 1e-3 * na * nb  # not trivially zero
+    assert abs(w1 - w0) < 1e-12 * na * nb
