@@ -487,17 +487,18 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
 // along z, multiplied by the exponential and transformed back, with all six
 // components of a tile (fixed ky, TX consecutive kx, every kz) held in
 // registers and transformed one after another through one exchange buffer:
-// thread (x, t) owns positions t + P*m of its column for the six components, which are exactly the frequencies its
-// forward transforms produce and its inverse transforms consume (mx_fft.cuh).
-// One read and one write of the spectrum replace three passes (z forward,
-// update, z inverse).  With TMAP the next tile is brought into a shared-memory
-// stage by the tensor copy engine while the current one is computed
-// With TMAP the tile's results leave through an output stage and a tensor
-// store.  Invariants of the updated state are
-// summed per thread in T over a tile, then per warp in a compensated (Kahan)
-// pair of T in shared memory, converted to FP64 at the end: no FP64 arithmetic
-// in the loop, where an FP64 instruction costs the pipe as much with one
-// active lane as with 32.
+// thread (x, t) owns positions t + P*m of its column for the six components,
+// which are exactly the frequencies its forward transforms produce and its
+// inverse transforms consume (mx_fft.cuh).  One read and one write of the
+// spectrum replace three passes (z forward, update, z inverse).
+// With TMAP a tile arrives by tensor copy in an input stage; once read, the
+// stage first holds the tile's coefficient-table entries (cp.async, during
+// the forward transforms), then takes the next tile while the update and the
+// inverse transforms run; the results leave through an output stage and a
+// tensor store.  Invariants of the updated state are summed per thread in T
+// over a tile, then per warp in a compensated (Kahan) pair of T in shared
+// memory, converted to FP64 at the end: no FP64 arithmetic in the loop, where
+// an FP64 instruction costs the pipe as much with one active lane as with 32.
 template <typename T, int N, int E, int TX>
 struct ZTile {
   static constexpr int P = N / E;
@@ -597,13 +598,8 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       for (int c = 0; c < 6; ++c)
 #pragma unroll
         for (int m = 0; m < E; ++m) v[c][m] = stage[ZT::stage_index(c, t + P * m, x)];
-      fence_proxy_async_smem();
       __syncthreads();  // every read of the stage is done (and the twiddles are in)
       pending = false;
-      if (threadIdx.x == 0 && tile + gridDim.x < ntiles) {
-        z_tile_copy<T, N, E, TX>(tmap, stage, full, tile + gridDim.x, ntx);
-        pending = true;
-      }
     } else {
 #pragma unroll
       for (int c = 0; c < 6; ++c)
@@ -612,8 +608,23 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       __syncthreads();  // twiddles
     }
     const int my = signed_index(y, g.ny);
+    // TMAP: the input stage is free until the next tile's copy; this thread's coefficient-table
+    // entries are copied into it (cp.async) while the forward transforms run
+    CoefT* cst = reinterpret_cast<CoefT*>(stage);
+    static_assert((size_t)E * ZT::NT * sizeof(CoefT) <= ZT::stage_bytes, "coefficients fit in the stage");
+    const bool staged = TMAP && tab != nullptr && ok;
+    if (staged) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int mz = signed_index(t + P * m, N);
+        cp_async_16n<sizeof(CoefT)>(cst + m * ZT::NT + threadIdx.x,
+                                    tab + (g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz));
+      }
+      cp_async_commit();
+    }
 #pragma unroll
     for (int c = 0; c < 6; c += ZT::NL) lines_fft<T, N, E, -1, 0, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
+    if (staged) cp_async_wait_all();
     T part[INV ? NSUM : 1];
 #pragma unroll
     for (int k = 0; k < (INV ? NSUM : 1); ++k) part[k] = (T)0;
@@ -624,7 +635,9 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
         const int mz = signed_index(t + P * m, N);
         const T kz = nuz * (T)mz;
         CoefT q;
-        if (tab) {
+        if (staged) {
+          q = cst[m * ZT::NT + threadIdx.x];
+        } else if (tab) {
           q = tab[g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz];
         } else {
           const double k2 = g.nu[0] * g.nu[0] * (double)col * col + g.nu[1] * g.nu[1] * (double)my * my +
@@ -637,6 +650,15 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
 #pragma unroll
         for (int c = 0; c < 3; ++c) v[c][m] = ee[c], v[c + 3][m] = hh[c];
         if constexpr (INV) add_densities<T>(part, col == 0 ? (T)1 : (T)2, kx, ky, kz, hh, ee, eps, mu);
+      }
+    }
+    if constexpr (TMAP) {
+      // the stage's coefficient reads are done: it takes the next tile (async proxy after generic)
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0 && tile + gridDim.x < ntiles) {
+        z_tile_copy<T, N, E, TX>(tmap, stage, full, tile + gridDim.x, ntx);
+        pending = true;
       }
     }
     if constexpr (INV) {
