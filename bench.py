@@ -555,6 +555,15 @@ def main():
     bytes_per_launch = pass_bytes(dom, grid, 4)
     achieved = bytes_per_launch / (dom_ms / dom_n / 1e3) / 1e9
     launches = int(sum(v[1] for v in prof.values()))
+    # every pass of the step against the same peak (algorithmic bytes / mean launch time)
+    per_pass = {}
+    for k, (k_ms, k_n) in prof.items():
+        if k in ("table", "gen") or not k_n:
+            continue
+        a_gbs = pass_bytes(k, grid, 4) / (k_ms / k_n / 1e3) / 1e9
+        per_pass[k] = {"kernel": KERNEL_NAMES.get(k, k), "ms_per_launch": k_ms / k_n,
+                       "launches_per_step": k_n / args.steps, "achieved_gbs": a_gbs, "frac": a_gbs / peak,
+                       "traffic": traffic_for(f"{k}_fp32_{grid}")}
     forms = {}
     name, e = form_entry("precision_fp32_literal", grid, mx.MX_FP32, mx.MX_FORM_LITERAL, ms, args.steps, prof, peak,
                          inv, world)
@@ -612,6 +621,7 @@ def main():
             "algorithmic_bytes_per_launch": bytes_per_launch,
         },
         "step_hbm_roofline_frac": forms["precision_fp32_literal"]["step_hbm_roofline_frac"],
+        "roofline_per_pass": per_pass,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
