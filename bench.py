@@ -415,6 +415,31 @@ def serve_run(torch, mx, duration=5.0, rate=200.0, seed=5, budget=32 << 30):
     }
 
 
+def cufft_comparison(torch, grid, steps=20, warmup=3):
+    """Timing comparison only (not part of the product): cuFFT through torch.fft, forward R2C and
+    inverse C2R of six FP32 fields of grid^3 per step, with no update or invariants."""
+    x = torch.randn(6, grid, grid, grid, device="cuda", dtype=torch.float32)
+    dims = (1, 2, 3)
+    for _ in range(warmup):
+        y = torch.fft.rfftn(x, dim=dims)
+        x = torch.fft.irfftn(y, s=(grid,) * 3, dim=dims)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        y = torch.fft.rfftn(x, dim=dims)
+        x = torch.fft.irfftn(y, s=(grid,) * 3, dim=dims)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    del x, y
+    torch.cuda.empty_cache()
+    return {"what": "cuFFT via torch.fft: rfftn + irfftn of six FP32 fields per step (transforms only, no update, "
+                    "no invariants); a timing comparison, not used by the library",
+            "ms_per_step": ms, "steps": steps}
+
+
 def cpu_baseline_sample(budget_s=15.0):
     """The FP64 oracle (numpy, as it stands) on the host cores: Alg. 1 + Alg. 2 at 128^3."""
     import synth
@@ -580,6 +605,7 @@ def main():
 
     e2e = e2e_run(torch, mx, grid, args.steps, stream)
     batched = None if args.no_secondary else batch_run(torch, mx, peak, min(args.steps, 100), args.warmup, stream)
+    comparison = None if args.no_secondary else {"cufft_transforms": cufft_comparison(torch, grid)}
     serve = None if (args.no_secondary or rank != 0) else serve_run(torch, mx)
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -629,6 +655,7 @@ def main():
         "forms": forms,
         "batched": batched,
         "serve": serve,
+        "comparison": comparison,
     }
     print(json.dumps(out), flush=True)
     if dist is not None:
