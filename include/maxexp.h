@@ -160,20 +160,26 @@ mx_status mx_read_invariants(mx_ctx* ctx, mx_invariants* out, long long max, lon
 mx_status mx_load_random_divfree(mx_ctx* ctx, unsigned long long seed, double sigma);
 
 /*
- * FFT schedule autotuner (no counterpart in the paper: it picks launch
- * shapes).  Each of the six transform passes of this grid shape (x R2C, y
- * forward, z forward, z inverse, y inverse, x C2R) is timed with every
- * candidate persistent grid (0, 1, 2, 4, 8 blocks per SM; 0 = one block per
- * tile) on the context's own work buffers; the fastest is kept in a
- * process-wide table keyed by (pass, precision, nx, ny, nz) and used by every
- * context of that shape.  Waits for the stream.  Skipped (MX_OK) while the
- * stream is being captured, or for a loaded literal-form context (its state
- * lives in the buffers the timing overwrites); a spectral-form context keeps
- * its state.  Untuned passes use 4 blocks per SM.
+ * FFT schedule autotuner (no counterpart in the paper: it picks kernels and
+ * launch shapes).  Each transform pass of this grid shape (x R2C, y forward,
+ * z forward, z inverse, y inverse, x C2R and, for a literal-form context with
+ * a fused z plan, the fused z pass) is timed on the context's own work
+ * buffers with every candidate schedule: the kernel variant (tiles moved by
+ * the bulk/tensor-copy engine where the layout allows, or per-thread loads
+ * with a register prefetch) and the persistent grid (1, 2, 4, 8 blocks per
+ * SM, 0 = one block per tile for the second variant; 1 or 2 for the fused z
+ * pass).  The fastest is kept in a process-wide table keyed by (pass,
+ * precision, nx, ny, nz) and used by every context of that shape.  Waits for
+ * the stream.  Skipped (MX_OK) while the stream is being captured, or for a
+ * loaded literal-form context (its state lives in the buffers the timing
+ * overwrites); a spectral-form context keeps its state.  Untuned passes use
+ * the copy-engine variant with 4 blocks per SM (fused z: 2).
  */
 mx_status mx_autotune(mx_ctx* ctx);
-/* The schedule in use: bps[0..5] = blocks per SM of the six passes (n >= 6). */
-mx_status mx_schedule(mx_ctx* ctx, int* bps, int n);
+/* The schedules in use, sched[0..6] for the seven passes in the order above
+ * (n >= 7): blocks per SM + 16 * variant (0: copy-engine tiles, 1: register
+ * prefetch). */
+mx_status mx_schedule(mx_ctx* ctx, int* sched, int n);
 
 /*
  * Batched form (no counterpart in the paper, which solves one problem at a

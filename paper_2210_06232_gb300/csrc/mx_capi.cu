@@ -203,24 +203,34 @@ template <typename T> using C2 = mx::cx<T>;
 
 // ------------------------------------------------------------ FFT autotuner
 //
-// Each FFT pass of a grid shape has a schedule: the persistent grid size in
-// blocks per SM (0 = one block per tile).  mx_autotune times the candidates
-// on the context's own buffers and keeps the fastest in a process-wide table
-// keyed by (pass, precision, grid shape); untuned passes use the default.
-enum Pass { P_X_R2C = 0, P_Y_FWD, P_Z_FWD, P_Z_INV, P_Y_INV, P_X_C2R, P_COUNT };
-constexpr int kCandidates[] = {0, 1, 2, 4, 8};
-constexpr int kDefaultBps = 4;
+// Each transform pass of a grid shape has a schedule: the kernel variant (0:
+// tiles brought in and out by the bulk/tensor-copy engine where the layout
+// allows, 1: per-thread loads with a register prefetch) and the persistent
+// grid size in blocks per SM (0 = one block per tile), coded as
+// bps + 16 * variant.  mx_autotune times the candidates on the context's own
+// buffers and keeps the fastest in a process-wide table keyed by (pass,
+// precision, grid shape); untuned passes use the default.
+enum Pass { P_X_R2C = 0, P_Y_FWD, P_Z_FWD, P_Z_INV, P_Y_INV, P_X_C2R, P_Z_FUSED, P_COUNT };
+constexpr int kCandidates[] = {1, 2, 4, 8, 16 + 0, 16 + 1, 16 + 2, 16 + 4, 16 + 8};
+constexpr int kFusedCandidates[] = {1, 2, 16 + 1, 16 + 2};  // at most 2 blocks per SM (partial sums)
+constexpr int kDefaultSchedule = 4;
+constexpr int kDefaultFused = 2;
 std::mutex g_tune_mu;
 std::map<long long, int> g_tune;
 
 long long tune_key(const mx_ctx* c, int pass) {
   return ((((long long)pass * 2 + c->prec) * 1024 + c->nx) * 1024 + c->ny) * 1024 + c->nz;
 }
-int pass_bps(const mx_ctx* c, int pass) {
+int pass_schedule(const mx_ctx* c, int pass) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tune.find(tune_key(c, pass));
-  return it == g_tune.end() ? kDefaultBps : it->second;
+  return it == g_tune.end() ? (pass == P_Z_FUSED ? kDefaultFused : kDefaultSchedule) : it->second;
 }
+int sched_bps(int code) { return code & 15; }
+bool sched_pipelined(int code) { return (code >> 4) == 0; }
+int pass_bps(const mx_ctx* c, int pass) { return sched_bps(pass_schedule(c, pass)); }
+// the completion counter turns the pipelined variants on (and is their timeout flag)
+unsigned* pass_pipe(const mx_ctx* c, int pass) { return sched_pipelined(pass_schedule(c, pass)) ? c->counter : nullptr; }
 
 // Event pair around one kernel launch when profiling is on.
 struct ProfScope {
@@ -256,18 +266,18 @@ cudaError_t forward3(mx_ctx* c, const T* e, const T* h, void* spec, bool with_z 
   {
     ProfScope ps(c, MX_K_X_R2C);
     err = mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, pass_bps(c, P_X_R2C),
-                              c->stream, c->counter);
+                              c->stream, pass_pipe(c, P_X_R2C));
   }
   if (err != cudaSuccess) return err;
   {
     ProfScope ps(c, MX_K_Y_FFT);
     err = mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, pass_bps(c, P_Y_FWD),
-                                c->stream, c->counter);
+                                c->stream, pass_pipe(c, P_Y_FWD));
   }
   if (err != cudaSuccess || !with_z) return err;
   ProfScope ps(c, MX_K_Z_FFT);
   return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, pass_bps(c, P_Z_FWD),
-                               c->stream, c->counter);
+                               c->stream, pass_pipe(c, P_Z_FWD));
 }
 
 template <typename T>
@@ -278,41 +288,60 @@ cudaError_t inverse3(mx_ctx* c, void* spec, T* e, T* h, bool with_z = true) {
   if (with_z) {
     ProfScope ps(c, MX_K_Z_FFT);
     err = mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, pass_bps(c, P_Z_INV),
-                                c->stream, c->counter);
+                                c->stream, pass_pipe(c, P_Z_INV));
   }
   if (err != cudaSuccess) return err;
   {
     ProfScope ps(c, MX_K_Y_FFT);
     err = mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, pass_bps(c, P_Y_INV),
-                                c->stream, c->counter);
+                                c->stream, pass_pipe(c, P_Y_INV));
   }
   if (err != cudaSuccess) return err;
   const double scale = 1.0 / (double)c->ns;
   ProfScope ps(c, MX_K_X_C2R);
   return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, scale, pass_bps(c, P_X_C2R),
-                             c->stream, c->counter);
+                             c->stream, pass_pipe(c, P_X_C2R));
 }
 
-// One launch of `pass` with schedule bps on the context's work buffers (contents are scratch).
 template <typename T>
-cudaError_t run_pass(mx_ctx* c, int pass, int bps) {
+cudaError_t ensure_table(mx_ctx* c, double t);
+
+// Grid of the fused z pass: bps blocks per SM over its tiles (at most the partial-sum slots).
+int zfused_grid(const mx_ctx* c, int bps) {
+  const int tx = std::max(1, mx::zfused_tile_cols(c->nz, c->prec == MX_FP64));
+  const long tiles = (long)c->ny * ((c->mx + tx - 1) / tx);
+  const long cap = std::min<long>((long)mx::num_sms() * std::max(bps, 1), c->pblocks);
+  return (int)std::min<long>(std::max<long>(tiles, 1), cap);
+}
+
+// One launch of `pass` with schedule `code` on the context's work buffers (contents are scratch).
+template <typename T>
+cudaError_t run_pass(mx_ctx* c, int pass, int code) {
   const long long rows = (long long)c->ny * c->nz;
   const size_t fb = (size_t)3 * c->ns * c->es;
   T* e = (T*)c->phys;
   T* h = (T*)((char*)c->phys + fb);
   C2<T>* s = (C2<T>*)c->spec;
+  const int bps = sched_bps(code);
+  unsigned* pipe = sched_pipelined(code) ? c->counter : nullptr;
   switch (pass) {
     case P_X_R2C:
-      return mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, bps, c->stream, c->counter);
-    case P_Y_FWD: return mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream, c->counter);
+      return mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, bps, c->stream, pipe);
+    case P_Y_FWD: return mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream, pipe);
     case P_Z_FWD:
-      return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream, c->counter);
+      return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream, pipe);
     case P_Z_INV:
-      return mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream, c->counter);
-    case P_Y_INV: return mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream, c->counter);
+      return mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream, pipe);
+    case P_Y_INV: return mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream, pipe);
     case P_X_C2R:
-      return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, 1.0, bps, c->stream,
-                                 c->counter);
+      return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, 1.0, bps, c->stream, pipe);
+    case P_Z_FUSED: {  // literal form: coefficients of an arbitrary step, invariants not recorded
+      cudaError_t err = ensure_table<T>(c, 0.01);
+      if (err != cudaSuccess) return err;
+      return mx::launch_z_fused<T>(coef_kind(c), s, c->g, c->tab, 0.01, (const mx::twv<T>*)c->twz + c->twz_zf,
+                                   zfused_grid(c, bps), sched_pipelined(code), c->partials, c->counter, nullptr,
+                                   c->stream);
+    }
   }
   return cudaErrorInvalidValue;
 }
@@ -327,25 +356,31 @@ mx_status tune_t(mx_ctx* c) {
   cudaEvent_t e0, e1;
   MX_CHECK(c, cudaEventCreate(&e0));
   MX_CHECK(c, cudaEventCreate(&e1));
+  const bool fused = c->form == MX_FORM_LITERAL && mx::zfused_supported(c->nz, c->prec == MX_FP64);
   for (int pass = 0; pass < P_COUNT; ++pass) {
+    if (pass == P_Z_FUSED && !fused) continue;
     {
       std::lock_guard<std::mutex> lock(g_tune_mu);
       if (g_tune.count(tune_key(c, pass))) continue;
     }
     float best = 1e30f;
-    int best_bps = kDefaultBps;
-    for (int bps : kCandidates) {
-      MX_CHECK(c, run_pass<T>(c, pass, bps));  // warm-up (module load, attributes)
+    int best_code = pass == P_Z_FUSED ? kDefaultFused : kDefaultSchedule;
+    const int* cand = pass == P_Z_FUSED ? kFusedCandidates : kCandidates;
+    const int ncand = pass == P_Z_FUSED ? (int)(sizeof(kFusedCandidates) / sizeof(int))
+                                        : (int)(sizeof(kCandidates) / sizeof(int));
+    for (int ci = 0; ci < ncand; ++ci) {
+      const int code = cand[ci];
+      MX_CHECK(c, run_pass<T>(c, pass, code));  // warm-up (module load, attributes)
       MX_CHECK(c, cudaEventRecord(e0, c->stream));
-      for (int r = 0; r < 3; ++r) MX_CHECK(c, run_pass<T>(c, pass, bps));
+      for (int r = 0; r < 3; ++r) MX_CHECK(c, run_pass<T>(c, pass, code));
       MX_CHECK(c, cudaEventRecord(e1, c->stream));
       MX_CHECK(c, cudaEventSynchronize(e1));
       float ms = 0.f;
       MX_CHECK(c, cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) best = ms, best_bps = bps;
+      if (ms < best) best = ms, best_code = code;
     }
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune[tune_key(c, pass)] = best_bps;
+    g_tune[tune_key(c, pass)] = best_code;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -466,10 +501,10 @@ mx_status step_t(mx_ctx* c, double h, long long nsteps, int every) {
         MX_CHECK(c, ensure_table<T>(c, h));
         {
           ProfScope ps(c, MX_K_ZFUSED);
-          const long tiles = (long)c->ny * ((c->mx + 3) / 4);
-          const int grid = (int)std::min<long>(std::max<long>(tiles, 1), c->pblocks);
+          const int code = pass_schedule(c, P_Z_FUSED);
           MX_CHECK(c, mx::launch_z_fused<T>(coef_kind(c), (C2<T>*)c->spec, c->g, c->tab, h, (const mx::twv<T>*)c->twz + c->twz_zf,
-                                            grid, c->partials, c->counter, record, c->stream));
+                                            zfused_grid(c, sched_bps(code)), sched_pipelined(code), c->partials,
+                                            c->counter, record, c->stream));
         }
         MX_CHECK(c, inverse3<T>(c, c->spec, e, hh, false));
       } else {
@@ -643,9 +678,9 @@ mx_status mx_autotune(mx_ctx* c) {
   return c->prec == MX_FP64 ? tune_t<double>(c) : tune_t<float>(c);
 }
 
-mx_status mx_schedule(mx_ctx* c, int* bps, int n) {
-  if (!c || !bps || n < P_COUNT) return MX_E_INVAL;
-  for (int p = 0; p < P_COUNT; ++p) bps[p] = pass_bps(c, p);
+mx_status mx_schedule(mx_ctx* c, int* sched, int n) {
+  if (!c || !sched || n < P_COUNT) return MX_E_INVAL;
+  for (int p = 0; p < P_COUNT; ++p) sched[p] = pass_schedule(c, p);
   return MX_OK;
 }
 

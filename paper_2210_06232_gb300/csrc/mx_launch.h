@@ -51,10 +51,13 @@ bool zfused_supported(int nz, bool fp64);
 // (0 when it has no plan for n); the twiddle tables are laid out for these plans.
 int fft_line_E(int n);
 int zfused_line_E(int n, bool fp64);
+// Columns per tile of the fused z pass for length n.
+int zfused_tile_cols(int n, bool fp64);
 template <typename T>
+// pipelined: tensor-copy tiles (when the layout allows), else per-thread loads and stores.
 cudaError_t launch_z_fused(int coef_kind, cx<T>* data, const GridParams& g, const void* tab, double t,
-                           const twv<T>* tw, int grid, double* partials, unsigned* counter, double* record,
-                           cudaStream_t s);
+                           const twv<T>* tw, int grid, bool pipelined, double* partials, unsigned* counter,
+                           double* record, cudaStream_t s);
 
 // Blocks used by the spectral pass for npts points (fixed per size: makes
 // the invariant reduction order independent of what else runs).

@@ -28,7 +28,7 @@ static bool z_tensor_map(CUtensorMap* m, const void* data, const GridParams& g) 
 
 template <typename T, int N, typename CoefT>
 static cudaError_t zf_n(cx<T>* data, const GridParams& g, const void* tab, double t, const twv<T>* tw, int grid,
-                        double* partials, unsigned* counter, double* record, cudaStream_t s) {
+                        bool pipelined, double* partials, unsigned* counter, double* record, cudaStream_t s) {
   constexpr int E = zf_E<T>(N);
   if constexpr (E == 0) {
     return cudaErrorInvalidValue;
@@ -43,7 +43,7 @@ static cudaError_t zf_n(cx<T>* data, const GridParams& g, const void* tab, doubl
     constexpr size_t smem_tma = 2 * ZT::stage_bytes + ZT::tw_bytes + ZT::exch_bytes + 16;
     if constexpr (smem_tma + ZT::static_bytes <= 232448) {  // shared memory of a block on sm_103a
       CUtensorMap m;
-      if (counter && z_tensor_map<T, N, E, TX>(&m, data, g)) {
+      if (pipelined && counter && z_tensor_map<T, N, E, TX>(&m, data, g)) {
         if (record) {
           auto k = k_z_fused_tma<T, N, E, TX, CoefT, true>;
           if ((err = set_smem(k, smem_tma)) != cudaSuccess) return err;
@@ -73,12 +73,13 @@ static cudaError_t zf_n(cx<T>* data, const GridParams& g, const void* tab, doubl
 bool zfused_supported(int nz, bool fp64) { return fp64 ? zf_E<double>(nz) > 0 : zf_E<float>(nz) > 0; }
 int fft_line_E(int n) { return fft_E(n); }
 int zfused_line_E(int n, bool fp64) { return fp64 ? zf_E<double>(n) : zf_E<float>(n); }
+int zfused_tile_cols(int n, bool fp64) { return fp64 ? zf_TX<double>(n) : zf_TX<float>(n); }
 
 template <typename T, typename CoefT>
 static cudaError_t zf_dispatch(cx<T>* data, const GridParams& g, const void* tab, double t, const twv<T>* tw, int grid,
-                               double* partials, unsigned* counter, double* record, cudaStream_t s) {
+                               bool pipelined, double* partials, unsigned* counter, double* record, cudaStream_t s) {
   switch (g.nz) {
-#define X(n) case n: return zf_n<T, n, CoefT>(data, g, tab, t, tw, grid, partials, counter, record, s);
+#define X(n) case n: return zf_n<T, n, CoefT>(data, g, tab, t, tw, grid, pipelined, partials, counter, record, s);
     MX_ZF_LENS(X)
 #undef X
   }
@@ -87,19 +88,19 @@ static cudaError_t zf_dispatch(cx<T>* data, const GridParams& g, const void* tab
 
 template <>
 cudaError_t launch_z_fused<float>(int coef_kind, float2* data, const GridParams& g, const void* tab, double t,
-                                  const float4* tw, int grid, double* partials, unsigned* counter, double* record,
+                                  const float4* tw, int grid, bool pipelined, double* partials, unsigned* counter, double* record,
                                   cudaStream_t s) {
-  if (coef_kind == 1) return zf_dispatch<float, CoefHL>(data, g, tab, t, tw, grid, partials, counter, record, s);
-  if (coef_kind == 3) return zf_dispatch<float, CoefHL>(data, g, nullptr, t, tw, grid, partials, counter, record, s);
+  if (coef_kind == 1) return zf_dispatch<float, CoefHL>(data, g, tab, t, tw, grid, pipelined, partials, counter, record, s);
+  if (coef_kind == 3) return zf_dispatch<float, CoefHL>(data, g, nullptr, t, tw, grid, pipelined, partials, counter, record, s);
   return cudaErrorInvalidValue;
 }
 
 template <>
 cudaError_t launch_z_fused<double>(int coef_kind, double2* data, const GridParams& g, const void* tab, double t,
-                                   const double2* tw, int grid, double* partials, unsigned* counter, double* record,
+                                   const double2* tw, int grid, bool pipelined, double* partials, unsigned* counter, double* record,
                                    cudaStream_t s) {
-  if (coef_kind == 0) return zf_dispatch<double, Coef<double>>(data, g, tab, t, tw, grid, partials, counter, record, s);
-  if (coef_kind == 2) return zf_dispatch<double, Coef<double>>(data, g, nullptr, t, tw, grid, partials, counter, record, s);
+  if (coef_kind == 0) return zf_dispatch<double, Coef<double>>(data, g, tab, t, tw, grid, pipelined, partials, counter, record, s);
+  if (coef_kind == 2) return zf_dispatch<double, Coef<double>>(data, g, nullptr, t, tw, grid, pipelined, partials, counter, record, s);
   return cudaErrorInvalidValue;
 }
 

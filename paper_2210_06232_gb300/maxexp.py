@@ -262,10 +262,14 @@ class Solver:
     def autotune(self):
         check(mx_autotune(self._h), "mx_autotune")
 
+    SCHEDULE_PASSES = ("x_r2c", "y_fwd", "z_fwd", "z_inv", "y_inv", "x_c2r", "z_fused")
+
     def schedule(self):
-        arr = (C.c_int * 6)()
-        check(mx_schedule(self._h, arr, 6), "mx_schedule")
-        return list(arr)
+        """{pass: (blocks per SM, 'copy-engine' | 'register-prefetch')} in use for this shape."""
+        arr = (C.c_int * 7)()
+        check(mx_schedule(self._h, arr, 7), "mx_schedule")
+        return {p: (v & 15, "copy-engine" if (v >> 4) == 0 else "register-prefetch")
+                for p, v in zip(self.SCHEDULE_PASSES, arr)}
 
     def profile(self, enable=True):
         check(mx_profile(self._h, 1 if enable else 0), "mx_profile")
