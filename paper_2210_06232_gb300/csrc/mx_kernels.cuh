@@ -215,31 +215,34 @@ __device__ __forceinline__ void add_densities(T* acc, T w, T kx, T ky, T kz, con
   const T kEr = kx * e[0].x + ky * e[1].x + kz * e[2].x, kEi = kx * e[0].y + ky * e[1].y + kz * e[2].y;
   const T kHr = kx * h[0].x + ky * h[1].x + kz * h[2].x, kHi = kx * h[0].y + ky * h[1].y + kz * h[2].y;
   const T kE2 = kEr * kEr + kEi * kEi, kH2 = kHr * kHr + kHi * kHi;
-  const T k2 = kx * kx + ky * ky + kz * kz;
+  const T kx2 = kx * kx, ky2 = ky * ky, kz2 = kz * kz;
+  const T k2 = kx2 + ky2 + kz2;
   // k . (Re U x Im U)
   const T ch = kx * (h[1].x * h[2].y - h[2].x * h[1].y) + ky * (h[2].x * h[0].y - h[0].x * h[2].y) +
                kz * (h[0].x * h[1].y - h[1].x * h[0].y);
   const T ce = kx * (e[1].x * e[2].y - e[2].x * e[1].y) + ky * (e[2].x * e[0].y - e[0].x * e[2].y) +
                kz * (e[0].x * e[1].y - e[1].x * e[0].y);
+  // material constants (loop invariants of every caller)
   const T ie = (T)1 / eps, im = (T)1 / mu;
+  const T c9e = ie * im * im, c9h = im * ie * ie, eps2 = eps * eps, mu2 = mu * mu;
   const T d0 = w * (mu * h2 + eps * e2);
   const T d1 = w * ((k2 * e2 - kE2) * im + (k2 * h2 - kH2) * ie);
   const T mim = w * (h[0].x * e[0].y - h[0].y * e[0].x + h[1].x * e[1].y - h[1].y * e[1].x + h[2].x * e[2].y - h[2].y * e[2].x);
   acc[0] += d0;
   acc[1] += d1;
-  acc[2] += kx * kx * d0;
-  acc[3] += ky * ky * d0;
-  acc[4] += kz * kz * d0;
-  acc[5] += kx * kx * d1;
-  acc[6] += ky * ky * d1;
-  acc[7] += kz * kz * d1;
+  acc[2] += kx2 * d0;
+  acc[3] += ky2 * d0;
+  acc[4] += kz2 * d0;
+  acc[5] += kx2 * d1;
+  acc[6] += ky2 * d1;
+  acc[7] += kz2 * d1;
   acc[8] += w * (ch * ie + ce * im);
-  acc[9] += w * k2 * (ce * ie * im * im + ch * im * ie * ie);
+  acc[9] += (w * k2) * (ce * c9e + ch * c9h);
   acc[10] += kx * mim;
   acc[11] += ky * mim;
   acc[12] += kz * mim;
-  acc[13] += w * eps * eps * kE2;
-  acc[14] += w * mu * mu * kH2;
+  acc[13] += (w * eps2) * kE2;
+  acc[14] += (w * mu2) * kH2;
 }
 
 // Block-wide FP64 reduction of NSUM values, then a deterministic grid
