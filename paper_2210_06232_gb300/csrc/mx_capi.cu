@@ -571,7 +571,7 @@ const char* mx_strerror(mx_status s) {
   switch (s) {
     case MX_OK: return "ok";
     case MX_E_INVAL: return "invalid argument";
-    case MX_E_UNSUPPORTED_N: return "unsupported grid size (need even N with N/2 (x) or N (y, z) of the form 2^a, 3*2^a, 5*2^a, <= 512)";
+    case MX_E_UNSUPPORTED_N: return "unsupported grid size (need nx/2 <= 256 and ny, nz <= 512, each of the form 2^a, 3*2^a or 5*2^a; nx even)";
     case MX_E_NOMEM: return "device allocation failed";
     case MX_E_CUDA: return "CUDA error";
     case MX_E_TIMEOUT: return "device wait timed out";

@@ -241,3 +241,27 @@ def test_symplectic_form_preserved_fp64(form):
     nb = np.sqrt(eps * np.sum(Eb ** 2) + mu * np.sum(Hb ** 2))
     assert abs(w0) > 1e-3 * na * nb  # not trivially zero
     assert abs(w1 - w0) < 1e-12 * na * nb
+
+
+# the longest lines of each radix family in every direction: x rows of 512 and 320 reals,
+# y and z lines of 384 (fused z plan of 3 * 2^a) and 320 (z without a fused plan)
+EDGE_GRIDS = [(512, 6, 8), (320, 4, 6), (8, 384, 6), (6, 8, 384), (8, 320, 10), (10, 6, 320)]
+
+
+@pytest.mark.parametrize("n", EDGE_GRIDS)
+@pytest.mark.parametrize("form", ["literal", "spectral"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_parity_longest_lines(n, form, prec):
+    mx = _mx()
+    g = synth.Grid(n, (0.0, 0.0, 0.0), (2.0, 3.0, 2.5))
+    E0, H0 = _fields(g, seed=sum(n), divfree=False)
+    eps, mu, h, steps = 1.3, 0.8, 0.021, 4
+    P = mx.MX_FP64 if prec == "fp64" else mx.MX_FP32
+    F = mx.MX_FORM_LITERAL if form == "literal" else mx.MX_FORM_SPECTRAL
+    E, H, inv = run_gpu(g, E0, H0, eps, mu, P, F, h, steps, every=1)
+    if form == "literal":
+        Eo, Ho = scheme.step(E0, H0, g.lo, g.hi, eps, mu, h, steps)
+    else:
+        Eo, Ho = scheme.solve(E0, H0, g.lo, g.hi, eps, mu, h * steps)
+    assert rel_l2(E, H, Eo, Ho) < (1e-12 if prec == "fp64" else 1e-5)
+    assert len(inv) == steps + 1
