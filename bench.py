@@ -185,10 +185,11 @@ KERNEL_SOURCES = {
     "x_r2c": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_xpass_tma.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
     "x_c2r": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_xpass_tma.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],
     "y_fft": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_strided_tma.cuh", "mx_tmap.h", "mx_fft_launch.cuh",
-              "mx_fft_f32.cu"],
+              "mx_fft_f32s.cu"],
     "z_fft": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_strided_tma.cuh", "mx_tmap.h", "mx_fft_launch.cuh",
-              "mx_fft_f32.cu"],
-    "z_fused": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_tmap.h", "mx_zfused.cu"],
+              "mx_fft_f32s.cu"],
+    "z_fused": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_tmap.h", "mx_fft_launch.cuh", "mx_zfused.cuh",
+                "mx_zfused_f32b.cu"],
     "spectral": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_spectral_tma.cuh", "mx_spectral.cu"],
 }
 
