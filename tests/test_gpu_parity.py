@@ -265,3 +265,33 @@ def test_parity_longest_lines(n, form, prec):
         Eo, Ho = scheme.solve(E0, H0, g.lo, g.hi, eps, mu, h * steps)
     assert rel_l2(E, H, Eo, Ho) < (1e-12 if prec == "fp64" else 1e-5)
     assert len(inv) == steps + 1
+
+
+def test_spectral_convergence_thm34_gpu():
+    """Thm 3.4 on the GPU (literal FP64, 10 steps): for smooth, non-band-limited data the error
+    against a 48^3 run decays faster than any power of N; the 48^3 reference is the GPU's too,
+    and every grid also matches the oracle."""
+    mx = _mx()
+
+    def fields(n):
+        g = synth.Grid((n, n, n))
+        x, y, z = g.mesh()
+        a = np.exp(np.sin(x)) * np.exp(np.cos(y))  # A = (0, 0, a cos z); E = curl A, H = 0
+        E = np.stack([a * (-np.sin(y)) * np.cos(z), -(a * np.cos(x)) * np.cos(z), 0 * x])
+        return g, E, 0 * E
+
+    h, steps = 0.07, 10
+    gF, EF, HF = fields(48)
+    EfT, HfT, _ = run_gpu(gF, EF, HF, 1.0, 1.0, mx.MX_FP64, mx.MX_FORM_LITERAL, h, steps, every=0)
+    errs = []
+    for n in (8, 12, 16, 24):
+        g, E, H = fields(n)
+        Et, Ht, _ = run_gpu(g, E, H, 1.0, 1.0, mx.MX_FP64, mx.MX_FORM_LITERAL, h, steps, every=0)
+        Eo, Ho = scheme.step(E, H, g.lo, g.hi, 1.0, 1.0, h, steps)
+        assert rel_l2(Et, Ht, Eo, Ho) < 1e-12
+        s = 48 // n
+        errs.append(np.sqrt(np.mean((Et - EfT[:, ::s, ::s, ::s]) ** 2) + np.mean((Ht - HfT[:, ::s, ::s, ::s]) ** 2)))
+    assert errs[-1] < 1e-6 * errs[0]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    rates = [np.log(errs[i] / errs[i + 1]) / np.log(n2 / n1) for i, (n1, n2) in enumerate([(8, 12), (12, 16), (16, 24)])]
+    assert rates[-1] > rates[0] > 2.0
