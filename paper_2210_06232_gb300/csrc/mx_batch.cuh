@@ -148,48 +148,6 @@ __device__ __forceinline__ int find_inst_s(const BatchArgs& a, const unsigned* s
 }
 __device__ __forceinline__ long long rec_slot(const BInst& b, long long N) { return N / b.every - b.n0 / b.every - 1; }
 
-// Transpose reduction of 16 values across a warp (value 15 is padding): after
-// levels with lane offsets 16, 8, 4, 2 each lane keeps one value index,
-// (lane >> 1) & 15, summed over its 16-lane group; the final xor-1 exchange
-// completes the sum over all 32 lanes.  16 shuffles instead of 16 x 5, and
-// the addition order is fixed.
-template <typename T>
-__device__ __forceinline__ T warp_transpose_sum16(T* v, int lane) {
-  // level 16: 8 exchanges
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const bool up = lane & 16;
-    const T send = up ? v[j] : v[j + 8];
-    const T recv = __shfl_xor_sync(0xffffffffu, send, 16);
-    v[j] = (up ? v[j + 8] : v[j]) + recv;
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const bool up = lane & 8;
-    const T send = up ? v[j] : v[j + 4];
-    const T recv = __shfl_xor_sync(0xffffffffu, send, 8);
-    v[j] = (up ? v[j + 4] : v[j]) + recv;
-  }
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const bool up = lane & 4;
-    const T send = up ? v[j] : v[j + 2];
-    const T recv = __shfl_xor_sync(0xffffffffu, send, 4);
-    v[j] = (up ? v[j + 2] : v[j]) + recv;
-  }
-  {
-    const bool up = lane & 2;
-    const T send = up ? v[0] : v[1];
-    const T recv = __shfl_xor_sync(0xffffffffu, send, 2);
-    v[0] = (up ? v[1] : v[0]) + recv;
-  }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
-// Value index held by `lane` after warp_transpose_sum16.
-__device__ __forceinline__ int transpose_index(int lane) {
-  return ((lane & 16) ? 8 : 0) + ((lane & 8) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
-}
-
 // Invariant records, a two-level fixed tree: segment j of an instance is the
 // sum of its chunk-warp partials [j*BT_SEG, (j+1)*BT_SEG) (one warp per
 // segment, lane-strided then a fixed shuffle tree); the record is the sum of

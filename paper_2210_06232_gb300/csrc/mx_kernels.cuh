@@ -245,6 +245,48 @@ __device__ __forceinline__ void add_densities(T* acc, T w, T kx, T ky, T kz, con
   acc[14] += (w * mu2) * kH2;
 }
 
+// Transpose reduction of 16 values across a warp (value 15 is padding): after
+// levels with lane offsets 16, 8, 4, 2 each lane keeps one value index,
+// (lane >> 1) & 15, summed over its 16-lane group; the final xor-1 exchange
+// completes the sum over all 32 lanes.  16 shuffles instead of 16 x 5, and
+// the addition order is fixed.
+template <typename T>
+__device__ __forceinline__ T warp_transpose_sum16(T* v, int lane) {
+  // level 16: 8 exchanges
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const bool up = lane & 16;
+    const T send = up ? v[j] : v[j + 8];
+    const T recv = __shfl_xor_sync(0xffffffffu, send, 16);
+    v[j] = (up ? v[j + 8] : v[j]) + recv;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const bool up = lane & 8;
+    const T send = up ? v[j] : v[j + 4];
+    const T recv = __shfl_xor_sync(0xffffffffu, send, 8);
+    v[j] = (up ? v[j + 4] : v[j]) + recv;
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const bool up = lane & 4;
+    const T send = up ? v[j] : v[j + 2];
+    const T recv = __shfl_xor_sync(0xffffffffu, send, 4);
+    v[j] = (up ? v[j + 2] : v[j]) + recv;
+  }
+  {
+    const bool up = lane & 2;
+    const T send = up ? v[0] : v[1];
+    const T recv = __shfl_xor_sync(0xffffffffu, send, 2);
+    v[0] = (up ? v[1] : v[0]) + recv;
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+// Value index held by `lane` after warp_transpose_sum16.
+__device__ __forceinline__ int transpose_index(int lane) {
+  return ((lane & 16) ? 8 : 0) + ((lane & 8) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
+}
+
 // Block-wide FP64 reduction of NSUM values, then a deterministic grid
 // reduction by the last block to finish: partials[block][NSUM] -> record.
 // The counter must be zero on entry; the last block resets it.
@@ -628,9 +670,9 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
 #pragma unroll
     for (int c = 0; c < 6; c += ZT::NL) lines_fft<T, N, E, -1, 0, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
     if (staged) cp_async_wait_all();
-    T part[INV ? NSUM : 1];
+    T part[INV ? 16 : 1];  // NSUM sums and a zero (warp_transpose_sum16)
 #pragma unroll
-    for (int k = 0; k < (INV ? NSUM : 1); ++k) part[k] = (T)0;
+    for (int k = 0; k < (INV ? 16 : 1); ++k) part[k] = (T)0;
     if (ok) {
       const T kx = nux * (T)col, ky = nuy * (T)my;
 #pragma unroll
@@ -665,16 +707,12 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       }
     }
     if constexpr (INV) {
-#pragma unroll
-      for (int k = 0; k < NSUM; ++k) {
-        T w = part[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        if (lane == 0) {  // hi + (-lo) carries the sum
-          const T yv = w - zlo[warp][k], tv = zhi[warp][k] + yv;
-          zlo[warp][k] = (tv - zhi[warp][k]) - yv;
-          zhi[warp][k] = tv;
-        }
+      const T w = warp_transpose_sum16(part, lane);
+      const int k = transpose_index(lane);
+      if ((lane & 1) == 0 && k < NSUM) {  // hi + (-lo) carries the sum
+        const T yv = w - zlo[warp][k], tv = zhi[warp][k] + yv;
+        zlo[warp][k] = (tv - zhi[warp][k]) - yv;
+        zhi[warp][k] = tv;
       }
     }
 #pragma unroll

@@ -83,9 +83,9 @@ __global__ void __launch_bounds__(TMA_THREADS, 2)
     const unsigned mx = (unsigned)g.mx, ny = (unsigned)g.ny;
     const float eps = g.epsf, mu = g.muf;
     const float nux = g.nuf[0], nuy = g.nuf[1], nuz = g.nuf[2];
-    float part[INV ? NSUM : 1];
+    float part[INV ? 16 : 1];  // NSUM sums and a zero (warp_transpose_sum16)
 #pragma unroll
-    for (int k = 0; k < (INV ? NSUM : 1); ++k) part[k] = 0.f;
+    for (int k = 0; k < (INV ? 16 : 1); ++k) part[k] = 0.f;
     int cnt = 0;
     unsigned i = 0;
     // position of this thread's two points in chunk c, and their table entries
@@ -134,6 +134,19 @@ __global__ void __launch_bounds__(TMA_THREADS, 2)
       for (int comp = 0; comp < 6; ++comp) v[comp] = st4[comp * (TMA_CH / 2)];
       fence_proxy_async_smem();
       mbar_arrive(&empty[s]);
+      if constexpr (INV) {
+        // every 16 chunks (32 points per thread in FP32) the warp's sums go to FP64; taken by all
+        // lanes alike, before the lanes past the last point leave the iteration
+        if (cnt == 16) {
+          const float w = warp_transpose_sum16(part, lane);
+          const int k = transpose_index(lane);
+          if ((lane & 1) == 0 && k < NSUM) wsum[warp * NSUM + k] += (double)w;
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) part[k2] = 0.f;
+          cnt = 0;
+        }
+        ++cnt;
+      }
       if (!live) continue;
       const float ky = nuy * (float)my, kz = nuz * (float)mz;
 #pragma unroll
@@ -167,28 +180,11 @@ __global__ void __launch_bounds__(TMA_THREADS, 2)
         for (int comp = 0; comp < 6; ++comp)
           __stcs(reinterpret_cast<float4*>(dst + (size_t)comp * comp_stride + p), v[comp]);
       }
-      if constexpr (INV) {
-        if (++cnt == 16) {  // 32 points per thread in FP32, then FP64 per warp
-#pragma unroll
-          for (int k = 0; k < NSUM; ++k) {
-            float w = part[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-            if (lane == 0) wsum[warp * NSUM + k] += (double)w;
-            part[k] = 0.f;
-          }
-          cnt = 0;
-        }
-      }
     }
     if constexpr (INV) {
-#pragma unroll
-      for (int k = 0; k < NSUM; ++k) {
-        float w = part[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        if (lane == 0) wsum[warp * NSUM + k] += (double)w;
-      }
+      const float w = warp_transpose_sum16(part, lane);
+      const int k = transpose_index(lane);
+      if ((lane & 1) == 0 && k < NSUM) wsum[warp * NSUM + k] += (double)w;
     }
   }
   if constexpr (INV) {
