@@ -531,7 +531,8 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
 // For the literal form: the spectrum after the x and y passes is transformed
 // along z, multiplied by the exponential and transformed back, with all six
 // components of a tile (fixed ky, TX consecutive kx, every kz) held in
-// registers and transformed one after another through one exchange buffer:
+// registers and transformed one after another through one exchange buffer (two
+// at a time with TMAP, see below):
 // thread (x, t) owns positions t + P*m of its column for the six components,
 // which are exactly the frequencies its forward transforms produce and its
 // inverse transforms consume (mx_fft.cuh).  One read and one write of the
@@ -540,7 +541,10 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
 // stage first holds the tile's coefficient-table entries (cp.async, during
 // the forward transforms), then takes the next tile while the update and the
 // inverse transforms run; the results leave through an output stage and a
-// tensor store.  Invariants of the updated state are summed per thread in T
+// tensor store.  Components are then transformed in pairs, which halves the
+// barriers: the second exchange buffer of the forward transforms is the input
+// stage past the coefficients, that of the inverse transforms the output stage
+// (idle until their results are written, once the previous store has read it).  Invariants of the updated state are summed per thread in T
 // over a tile, then per warp in a compensated (Kahan) pair of T in shared
 // memory, converted to FP64 at the end: no FP64 arithmetic in the loop, where
 // an FP64 instruction costs the pipe as much with one active lane as with 32.
@@ -551,7 +555,7 @@ struct ZTile {
   static constexpr int ZC = N / NZC;           // z rows per box
   static constexpr size_t stage_bytes = (size_t)6 * N * TX * sizeof(cx<T>);
   static constexpr int NT = P * TX;  // threads
-  static constexpr int NL = 1;       // components transformed together (exchange buffers)
+  static constexpr int NL = 1;       // components per exchange buffer of this size (pairs: see above)
   static constexpr size_t exch_bytes = (size_t)NL * strided_rows(N) * TX * sizeof(cx<T>);
   static constexpr size_t tw_bytes = (size_t)N * sizeof(twv<T>);
   // static shared memory of the kernel: compensated sums and the block reduction
@@ -598,7 +602,8 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
   constexpr int P = N / E;
   constexpr int LS = strided_rows(N) * TX;  // exchange buffer of one component (TX lines side by side)
   extern __shared__ __align__(128) unsigned char zsmraw[];
-  // [input stage, output stage (TMAP only)][twiddles][exchange buffer][mbarrier]
+  // [input stage, output stage (TMAP only)][twiddles][exchange buffer][mbarrier]; the stages also
+  // serve as second exchange buffers
   C* stage = reinterpret_cast<C*>(zsmraw);
   C* ostage = reinterpret_cast<C*>(zsmraw + ZT::stage_bytes);
   twv<T>* tw = reinterpret_cast<twv<T>*>(zsmraw + (TMAP ? 2 * ZT::stage_bytes : 0));
@@ -667,8 +672,16 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       }
       cp_async_commit();
     }
+    if constexpr (TMAP && (size_t)E * ZT::NT * sizeof(CoefT) + ZT::exch_bytes <= ZT::stage_bytes) {
+      // two components at a time: the second exchange buffer is the input stage past the coefficients
+      C* xb2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(stage) + (size_t)E * ZT::NT * sizeof(CoefT));
+      const int ls2 = (int)(xb2 - sm);
 #pragma unroll
-    for (int c = 0; c < 6; c += ZT::NL) lines_fft<T, N, E, -1, 0, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
+      for (int c = 0; c < 6; c += 2) lines_fft<T, N, E, -1, 0, 2>(v + c, sm + x, TX, ls2, t, tw);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; c += ZT::NL) lines_fft<T, N, E, -1, 0, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
+    }
     if (staged) cp_async_wait_all();
     T part[INV ? 16 : 1];  // NSUM sums and a zero (warp_transpose_sum16)
 #pragma unroll
@@ -700,6 +713,9 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
     if constexpr (TMAP) {
       // the stage's coefficient reads are done: it takes the next tile (async proxy after generic)
       fence_proxy_async_smem();
+      // the previous tile's store has read the output stage: it is the inverse transforms' second
+      // exchange buffer
+      if (threadIdx.x == 0) bulk_wait_read_all();
       __syncthreads();
       if (threadIdx.x == 0 && tile + gridDim.x < ntiles) {
         z_tile_copy<T, N, E, TX>(tmap, stage, full, tile + gridDim.x, ntx);
@@ -715,12 +731,19 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
         zhi[warp][k] = tv;
       }
     }
+    if constexpr (TMAP) {
+      // two components at a time: the second exchange buffer is the output stage
+      static_assert(ZT::exch_bytes <= ZT::stage_bytes, "an exchange buffer fits in the output stage");
+      const int ls2 = (int)(ostage - sm);
 #pragma unroll
-    for (int c = 0; c < 6; c += ZT::NL) lines_fft<T, N, E, +1, 0, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
+      for (int c = 0; c < 6; c += 2) lines_fft<T, N, E, +1, 0, 2>(v + c, sm + x, TX, ls2, t, tw);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; c += ZT::NL) lines_fft<T, N, E, +1, 0, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
+    }
     if constexpr (TMAP) {
       // through the output stage and the tensor-copy engine (it drops the columns past Mx)
-      if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tile's store has read the stage
-      __syncthreads();
+      __syncthreads();  // the inverse transforms' exchange reads of the output stage are done
 #pragma unroll
       for (int c = 0; c < 6; ++c)
 #pragma unroll
