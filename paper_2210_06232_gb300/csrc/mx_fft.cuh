@@ -243,8 +243,16 @@ __host__ __device__ constexpr int line_bar(int P, int wide) { return (P <= 32 &&
 
 // NL lines at once (v[l][m]; line l exchanges through sm + l * LS): the lines
 // share the barriers and each twiddle load, and their butterflies interleave.
-template <typename T, int N, int E, int DIR, int NBAR, int NL, int NS = 1>
-__device__ __forceinline__ void lines_fft(cx<T> (*v)[E], cx<T>* sm, int SS, int LS, int t, const twv<T>* tw) {
+// PP: exchanges alternate between sm (even exchange index IX) and sm2 (odd), so
+// that an exchange need not wait for the readers of the one before it: the
+// barrier after the previous exchange's writes already orders them.  The first
+// exchange of a transform keeps its leading barrier unless the exchange count
+// is even, in which case the caller guarantees that the previous transform
+// also ran with PP on the same sm and sm2 (its last exchange used sm2) or that
+// a barrier has passed since sm was last read.
+template <typename T, int N, int E, int DIR, int NBAR, int NL, int NS = 1, int IX = 0, bool PP = false>
+__device__ __forceinline__ void lines_fft(cx<T> (*v)[E], cx<T>* sm, int SS, int LS, int t, const twv<T>* tw,
+                                          cx<T>* sm2 = nullptr) {
   if constexpr (NS < N) {
     constexpr int P = N / E;
     constexpr int R = pick_radix(N / NS, E);
@@ -267,7 +275,9 @@ __device__ __forceinline__ void lines_fft(cx<T> (*v)[E], cx<T>* sm, int SS, int 
       for (int l = 0; l < NL; ++l) bfly<R, DIR, B>(v[l] + b);
     }
     if constexpr (NS * R < N) {
-      fft_bar<NBAR>();  // previous readers of sm are done
+      cx<T>* xb = (PP && (IX & 1)) ? sm2 : sm;
+      constexpr int NX = num_stages(N, E) - 1;  // exchanges per transform
+      if constexpr (!(PP && (IX > 0 || NX % 2 == 0))) fft_bar<NBAR>();  // previous readers of xb are done
 #pragma unroll
       for (int b = 0; b < B; ++b) {
         const int j = t + P * b;
@@ -276,14 +286,14 @@ __device__ __forceinline__ void lines_fft(cx<T> (*v)[E], cx<T>* sm, int SS, int 
 #pragma unroll
         for (int l = 0; l < NL; ++l)
 #pragma unroll
-          for (int r = 0; r < R; ++r) sm[l * LS + xoff(base + r * NS, SS)] = v[l][b + r * B];
+          for (int r = 0; r < R; ++r) xb[l * LS + xoff(base + r * NS, SS)] = v[l][b + r * B];
       }
       fft_bar<NBAR>();
 #pragma unroll
       for (int l = 0; l < NL; ++l)
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[l][m] = sm[l * LS + xoff(t + P * m, SS)];
-      lines_fft<T, N, E, DIR, NBAR, NL, NS * R>(v, sm, SS, LS, t, tw);
+        for (int m = 0; m < E; ++m) v[l][m] = xb[l * LS + xoff(t + P * m, SS)];
+      lines_fft<T, N, E, DIR, NBAR, NL, NS * R, IX + 1, PP>(v, sm, SS, LS, t, tw, sm2);
     }
   }
 }

@@ -543,8 +543,10 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
 // inverse transforms run; the results leave through an output stage and a
 // tensor store.  Components are then transformed in pairs, which halves the
 // barriers: the second exchange buffer of the forward transforms is the input
-// stage past the coefficients, that of the inverse transforms the output stage
-// (idle until their results are written, once the previous store has read it).  Invariants of the updated state are summed per thread in T
+// stage past the coefficients; the inverse transforms exchange through four
+// buffers in the output stage (idle until their results are written, once the
+// previous store has read it), alternating between two pairs so that an
+// exchange has a single barrier.  Invariants of the updated state are summed per thread in T
 // over a tile, then per warp in a compensated (Kahan) pair of T in shared
 // memory, converted to FP64 at the end: no FP64 arithmetic in the loop, where
 // an FP64 instruction costs the pipe as much with one active lane as with 32.
@@ -659,16 +661,21 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
     }
     const int my = signed_index(y, g.ny);
     // TMAP: the input stage is free until the next tile's copy; this thread's coefficient-table
-    // entries are copied into it (cp.async) while the forward transforms run
-    CoefT* cst = reinterpret_cast<CoefT*>(stage);
+    // entries are copied into it (cp.async) while the forward transforms run, as planes of 16-byte
+    // pieces (piece h of entry m of thread i at cpl[(h E + m) NT + i]), so that a warp's copies and
+    // reads of one piece are 512 contiguous bytes
+    constexpr int NPC = (int)(sizeof(CoefT) / 16);
+    static_assert(sizeof(CoefT) % 16 == 0, "coefficient entries are whole 16-byte pieces");
+    float4* cpl = reinterpret_cast<float4*>(stage);
     static_assert((size_t)E * ZT::NT * sizeof(CoefT) <= ZT::stage_bytes, "coefficients fit in the stage");
     const bool staged = TMAP && tab != nullptr && ok;
     if (staged) {
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const int mz = signed_index(t + P * m, N);
-        cp_async_16n<sizeof(CoefT)>(cst + m * ZT::NT + threadIdx.x,
-                                    tab + (g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz));
+        const float4* src = reinterpret_cast<const float4*>(tab + (g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz));
+#pragma unroll
+        for (int h = 0; h < NPC; ++h) cp_async_16n<16>(cpl + (h * E + m) * ZT::NT + threadIdx.x, src + h);
       }
       cp_async_commit();
     }
@@ -694,7 +701,13 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
         const T kz = nuz * (T)mz;
         CoefT q;
         if (staged) {
-          q = cst[m * ZT::NT + threadIdx.x];
+          union {
+            CoefT c;
+            float4 f[NPC];
+          } u;
+#pragma unroll
+          for (int h = 0; h < NPC; ++h) u.f[h] = cpl[(h * E + m) * ZT::NT + threadIdx.x];
+          q = u.c;
         } else if (tab) {
           q = tab[g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz];
         } else {
@@ -732,11 +745,18 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       }
     }
     if constexpr (TMAP) {
-      // two components at a time: the second exchange buffer is the output stage
+      // two components at a time through the output stage: exchanges alternate between two pairs
+      // of buffers there, so that none waits for the readers of the one before it
       static_assert(ZT::exch_bytes <= ZT::stage_bytes, "an exchange buffer fits in the output stage");
-      const int ls2 = (int)(ostage - sm);
+      if constexpr (4 * ZT::exch_bytes <= ZT::stage_bytes) {
 #pragma unroll
-      for (int c = 0; c < 6; c += 2) lines_fft<T, N, E, +1, 0, 2>(v + c, sm + x, TX, ls2, t, tw);
+        for (int c = 0; c < 6; c += 2)
+          lines_fft<T, N, E, +1, 0, 2, 1, 0, true>(v + c, ostage + x, TX, LS, t, tw, ostage + 2 * LS + x);
+      } else {
+        const int ls2 = (int)(ostage - sm);
+#pragma unroll
+        for (int c = 0; c < 6; c += 2) lines_fft<T, N, E, +1, 0, 2>(v + c, sm + x, TX, ls2, t, tw);
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < 6; c += ZT::NL) lines_fft<T, N, E, +1, 0, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
