@@ -165,21 +165,30 @@ mx_status mx_load_random_divfree(mx_ctx* ctx, unsigned long long seed, double si
  * z forward, z inverse, y inverse, x C2R and, for a literal-form context with
  * a fused z plan, the fused z pass) is timed on the context's own work
  * buffers with every candidate schedule: the kernel variant (tiles moved by
- * the bulk/tensor-copy engine where the layout allows, or per-thread loads
- * with a register prefetch) and the persistent grid (1, 2, 4, 8 blocks per
- * SM, 0 = one block per tile for the second variant; 1 or 2 for the fused z
- * pass).  The fastest is kept in a process-wide table keyed by (pass,
- * precision, nx, ny, nz) and used by every context of that shape.  Waits for
- * the stream.  Skipped (MX_OK) while the stream is being captured, or for a
- * loaded literal-form context (its state lives in the buffers the timing
- * overwrites); a spectral-form context keeps its state.  Untuned passes use
- * the copy-engine variant with 4 blocks per SM (fused z: 2).
+ * the bulk/tensor-copy engine where the layout allows; per-thread loads with
+ * a register prefetch; for the y and z passes also the copy engine with two
+ * input stages that double as exchange buffers) and the persistent grid (1,
+ * 2, 4, 8 blocks per SM, 0 = one block per tile for the second variant; 1 or
+ * 2 for the fused z pass).  The fastest is kept in a process-wide table keyed
+ * by (pass, precision, nx, ny, nz) and used by every context of that shape.
+ * Waits for the stream.  Skipped (MX_OK) while the stream is being captured,
+ * or for a loaded literal-form context (its state lives in the buffers the
+ * timing overwrites); a spectral-form context keeps its state.  Untuned
+ * passes use the copy-engine variant with 4 blocks per SM (y and z passes of
+ * lines of 512 or more: the two-stage variant; fused z: 2 blocks per SM).
  */
 mx_status mx_autotune(mx_ctx* ctx);
 /* The schedules in use, sched[0..6] for the seven passes in the order above
  * (n >= 7): blocks per SM + 16 * variant (0: copy-engine tiles, 1: register
- * prefetch). */
+ * prefetch, 2: two-stage copy-engine tiles). */
 mx_status mx_schedule(mx_ctx* ctx, int* sched, int n);
+/* Set the schedules of this grid shape and precision (the process-wide table
+ * mx_autotune fills), sched[0..6] coded as mx_schedule reports them, for every
+ * context of the shape: a tuned table saved earlier, or one variant forced for
+ * a test.  MX_E_INVAL (nothing set) for an unknown variant, the two-stage
+ * variant on a pass other than y and z, a copy-engine variant with 0 blocks per
+ * SM, or a fused z pass with other than 1 or 2 blocks per SM. */
+mx_status mx_set_schedule(mx_ctx* ctx, const int* sched, int n);
 
 /*
  * Batched form (no counterpart in the paper, which solves one problem at a

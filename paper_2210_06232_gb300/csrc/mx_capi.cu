@@ -205,15 +205,18 @@ template <typename T> using C2 = mx::cx<T>;
 //
 // Each transform pass of a grid shape has a schedule: the kernel variant (0:
 // tiles brought in and out by the bulk/tensor-copy engine where the layout
-// allows, 1: per-thread loads with a register prefetch) and the persistent
-// grid size in blocks per SM (0 = one block per tile), coded as
+// allows, 1: per-thread loads with a register prefetch, 2: strided passes
+// only, as 0 with two input stages that double as exchange buffers) and the
+// persistent grid size in blocks per SM (0 = one block per tile), coded as
 // bps + 16 * variant.  mx_autotune times the candidates on the context's own
 // buffers and keeps the fastest in a process-wide table keyed by (pass,
 // precision, grid shape); untuned passes use the default.
 enum Pass { P_X_R2C = 0, P_Y_FWD, P_Z_FWD, P_Z_INV, P_Y_INV, P_X_C2R, P_Z_FUSED, P_COUNT };
 constexpr int kCandidates[] = {1, 2, 4, 8, 16 + 0, 16 + 1, 16 + 2, 16 + 4, 16 + 8};
+constexpr int kStridedCandidates[] = {1, 2, 4, 8, 16 + 0, 16 + 1, 16 + 2, 16 + 4, 16 + 8, 32 + 1, 32 + 2, 32 + 4};
 constexpr int kFusedCandidates[] = {1, 2, 16 + 1, 16 + 2};  // at most 2 blocks per SM (partial sums)
 constexpr int kDefaultSchedule = 4;
+constexpr int kDefaultLongStrided = 32 + 4;  // strided passes of lines of 512 and more
 constexpr int kDefaultFused = 2;
 std::mutex g_tune_mu;
 std::map<long long, int> g_tune;
@@ -221,16 +224,24 @@ std::map<long long, int> g_tune;
 long long tune_key(const mx_ctx* c, int pass) {
   return ((((long long)pass * 2 + c->prec) * 1024 + c->nx) * 1024 + c->ny) * 1024 + c->nz;
 }
+bool strided_pass(int pass) { return pass == P_Y_FWD || pass == P_Z_FWD || pass == P_Z_INV || pass == P_Y_INV; }
+int default_schedule(const mx_ctx* c, int pass) {
+  if (pass == P_Z_FUSED) return kDefaultFused;
+  const int len = (pass == P_Y_FWD || pass == P_Y_INV) ? c->ny : c->nz;
+  return strided_pass(pass) && len >= 512 ? kDefaultLongStrided : kDefaultSchedule;
+}
 int pass_schedule(const mx_ctx* c, int pass) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tune.find(tune_key(c, pass));
-  return it == g_tune.end() ? (pass == P_Z_FUSED ? kDefaultFused : kDefaultSchedule) : it->second;
+  return it == g_tune.end() ? default_schedule(c, pass) : it->second;
 }
 int sched_bps(int code) { return code & 15; }
-bool sched_pipelined(int code) { return (code >> 4) == 0; }
+bool sched_pipelined(int code) { return (code >> 4) != 1; }
+bool sched_dbuf(int code) { return (code >> 4) == 2; }
 int pass_bps(const mx_ctx* c, int pass) { return sched_bps(pass_schedule(c, pass)); }
 // the completion counter turns the pipelined variants on (and is their timeout flag)
 unsigned* pass_pipe(const mx_ctx* c, int pass) { return sched_pipelined(pass_schedule(c, pass)) ? c->counter : nullptr; }
+bool pass_dbuf(const mx_ctx* c, int pass) { return sched_dbuf(pass_schedule(c, pass)); }
 
 // Event pair around one kernel launch when profiling is on.
 struct ProfScope {
@@ -272,12 +283,12 @@ cudaError_t forward3(mx_ctx* c, const T* e, const T* h, void* spec, bool with_z 
   {
     ProfScope ps(c, MX_K_Y_FFT);
     err = mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, pass_bps(c, P_Y_FWD),
-                                c->stream, pass_pipe(c, P_Y_FWD));
+                                c->stream, pass_pipe(c, P_Y_FWD), pass_dbuf(c, P_Y_FWD));
   }
   if (err != cudaSuccess || !with_z) return err;
   ProfScope ps(c, MX_K_Z_FFT);
   return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, pass_bps(c, P_Z_FWD),
-                               c->stream, pass_pipe(c, P_Z_FWD));
+                               c->stream, pass_pipe(c, P_Z_FWD), pass_dbuf(c, P_Z_FWD));
 }
 
 template <typename T>
@@ -288,13 +299,13 @@ cudaError_t inverse3(mx_ctx* c, void* spec, T* e, T* h, bool with_z = true) {
   if (with_z) {
     ProfScope ps(c, MX_K_Z_FFT);
     err = mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, pass_bps(c, P_Z_INV),
-                                c->stream, pass_pipe(c, P_Z_INV));
+                                c->stream, pass_pipe(c, P_Z_INV), pass_dbuf(c, P_Z_INV));
   }
   if (err != cudaSuccess) return err;
   {
     ProfScope ps(c, MX_K_Y_FFT);
     err = mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, pass_bps(c, P_Y_INV),
-                                c->stream, pass_pipe(c, P_Y_INV));
+                                c->stream, pass_pipe(c, P_Y_INV), pass_dbuf(c, P_Y_INV));
   }
   if (err != cudaSuccess) return err;
   const double scale = 1.0 / (double)c->ns;
@@ -324,15 +335,20 @@ cudaError_t run_pass(mx_ctx* c, int pass, int code) {
   C2<T>* s = (C2<T>*)c->spec;
   const int bps = sched_bps(code);
   unsigned* pipe = sched_pipelined(code) ? c->counter : nullptr;
+  const bool dbuf = sched_dbuf(code);
   switch (pass) {
     case P_X_R2C:
       return mx::launch_x_r2c<T>(c->mx, e, h, s, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, bps, c->stream, pipe);
-    case P_Y_FWD: return mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream, pipe);
+    case P_Y_FWD:
+      return mx::launch_strided<T>(c->ny, -1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream, pipe, dbuf);
     case P_Z_FWD:
-      return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream, pipe);
+      return mx::launch_strided<T>(c->nz, -1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream, pipe,
+                                   dbuf);
     case P_Z_INV:
-      return mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream, pipe);
-    case P_Y_INV: return mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream, pipe);
+      return mx::launch_strided<T>(c->nz, +1, s, (long)c->mx * c->ny, 6, (const mx::twv<T>*)c->twz, bps, c->stream, pipe,
+                                   dbuf);
+    case P_Y_INV:
+      return mx::launch_strided<T>(c->ny, +1, s, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy, bps, c->stream, pipe, dbuf);
     case P_X_C2R:
       return mx::launch_x_c2r<T>(c->mx, s, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx, 1.0, bps, c->stream, pipe);
     case P_Z_FUSED: {  // literal form: coefficients of an arbitrary step, invariants not recorded
@@ -364,10 +380,11 @@ mx_status tune_t(mx_ctx* c) {
       if (g_tune.count(tune_key(c, pass))) continue;
     }
     float best = 1e30f;
-    int best_code = pass == P_Z_FUSED ? kDefaultFused : kDefaultSchedule;
-    const int* cand = pass == P_Z_FUSED ? kFusedCandidates : kCandidates;
-    const int ncand = pass == P_Z_FUSED ? (int)(sizeof(kFusedCandidates) / sizeof(int))
-                                        : (int)(sizeof(kCandidates) / sizeof(int));
+    int best_code = default_schedule(c, pass);
+    const int* cand = pass == P_Z_FUSED ? kFusedCandidates : strided_pass(pass) ? kStridedCandidates : kCandidates;
+    const int ncand = pass == P_Z_FUSED     ? (int)(sizeof(kFusedCandidates) / sizeof(int))
+                      : strided_pass(pass) ? (int)(sizeof(kStridedCandidates) / sizeof(int))
+                                           : (int)(sizeof(kCandidates) / sizeof(int));
     for (int ci = 0; ci < ncand; ++ci) {
       const int code = cand[ci];
       MX_CHECK(c, run_pass<T>(c, pass, code));  // warm-up (module load, attributes)
@@ -681,6 +698,20 @@ mx_status mx_autotune(mx_ctx* c) {
 mx_status mx_schedule(mx_ctx* c, int* sched, int n) {
   if (!c || !sched || n < P_COUNT) return MX_E_INVAL;
   for (int p = 0; p < P_COUNT; ++p) sched[p] = pass_schedule(c, p);
+  return MX_OK;
+}
+
+mx_status mx_set_schedule(mx_ctx* c, const int* sched, int n) {
+  if (!c || !sched || n < P_COUNT) return MX_E_INVAL;
+  for (int p = 0; p < P_COUNT; ++p) {
+    const int code = sched[p], bps = code & 15, variant = code >> 4;
+    if (code < 0 || variant > 2) return MX_E_INVAL;
+    if (variant == 2 && !strided_pass(p)) return MX_E_INVAL;
+    if (p == P_Z_FUSED && (variant > 1 || bps < 1 || bps > 2)) return MX_E_INVAL;  // partial-sum slots
+    if (variant != 1 && bps == 0) return MX_E_INVAL;  // copy-engine variants are persistent
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (int p = 0; p < P_COUNT; ++p) g_tune[tune_key(c, p)] = sched[p];
   return MX_OK;
 }
 

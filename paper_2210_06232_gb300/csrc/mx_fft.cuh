@@ -206,7 +206,12 @@ __host__ __device__ constexpr int tw_len(int N, int E) { return tw_stage_off(N, 
 // NBAR < 0 uses __syncwarp() (each line within one warp), NBAR == 0
 // __syncthreads(), NBAR > 0 the named barrier of this thread's group of NBAR
 // (warp-specialised kernels whose producer warp is busy).
-__device__ __forceinline__ int xoff(int p, int SS) { return SS == 1 ? p + (p >> 4) : (p + (p >> 3)) * SS; }
+// SS < 0: rows of -SS values with no padding, row p stored at p ^ ((p >> 3) & 1),
+// which puts rows 8 apart (written together at stride R = 8) on alternate halves
+// of the banks; the buffer is then exactly N * -SS values (N a multiple of 16).
+__device__ __forceinline__ int xoff(int p, int SS) {
+  return SS == 1 ? p + (p >> 4) : SS > 0 ? (p + (p >> 3)) * SS : (p ^ ((p >> 3) & 1)) * -SS;
+}
 // Exchange-buffer length (complex values) of one contiguous line of length n.
 __host__ __device__ constexpr int line_buf(int n) { return n + (n >> 4) + 1; }
 // Rows of the exchange buffer of interleaved lines (SS > 1): one padding row every 8.

@@ -96,7 +96,7 @@ static cudaError_t x_c2r_n(const cx<T>* in, T* e, T* h, long rows3, long nrows, 
 
 template <typename T, int N, int DIR>
 static cudaError_t strided_n(cx<T>* data, long inner, long outer, const twv<T>* tw, int bps, cudaStream_t s,
-                             unsigned* counter) {
+                             unsigned* counter, bool dbuf) {
   constexpr int E = fft_E(N), TX = fft_TX(N), P = N / E;
   static_assert(plan_ok(N, E), "plan");
   const long tiles = (inner + TX - 1) / TX * outer;
@@ -108,6 +108,17 @@ static cudaError_t strided_n(cx<T>* data, long inner, long outer, const twv<T>* 
     const cuuint64_t dim[3] = {(cuuint64_t)(2 * inner), (cuuint64_t)N, (cuuint64_t)outer};
     const cuuint32_t box[3] = {(cuuint32_t)(2 * TX), (cuuint32_t)ST::ZC, 1};
     if (counter && tensor_map(&m, (int)sizeof(T), 3, data, dim, box)) {
+      if constexpr (N % 16 == 0 && STile2<T, N, E, TX>::smem <= 232448) {
+        if (dbuf) {
+          auto k = k_fft_strided_tma2<T, N, E, TX, DIR>;
+          constexpr size_t smem2 = STile2<T, N, E, TX>::smem;
+          cudaError_t err = set_smem(k, smem2);
+          if (err != cudaSuccess) return err;
+          const long blocks = persistent_grid(tiles, bps > 0 ? bps : 1);
+          k<<<(unsigned)blocks, P * TX, smem2, s>>>(inner, outer, tw, counter, m);
+          return cudaGetLastError();
+        }
+      }
       auto k = k_fft_strided_tma<T, N, E, TX, DIR>;
       cudaError_t err = set_smem(k, ST::smem);
       if (err != cudaSuccess) return err;
@@ -151,17 +162,17 @@ cudaError_t launch_x_c2r(int M, const cx<T>* in, T* e, T* h, long rows3, long nr
 
 template <typename T>
 cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const twv<T>* tw, int bps,
-                           cudaStream_t s, unsigned* counter) {
+                           cudaStream_t s, unsigned* counter, bool dbuf) {
   if (inner <= 0 || outer <= 0 || N == 1) return cudaSuccess;
   if (dir < 0) {
     switch (N) {
-#define X(n) case n: return strided_n<T, n, -1>(data, inner, outer, tw, bps, s, counter);
+#define X(n) case n: return strided_n<T, n, -1>(data, inner, outer, tw, bps, s, counter, dbuf);
       MX_FOR_EACH_LEN(X)
 #undef X
     }
   } else {
     switch (N) {
-#define X(n) case n: return strided_n<T, n, +1>(data, inner, outer, tw, bps, s, counter);
+#define X(n) case n: return strided_n<T, n, +1>(data, inner, outer, tw, bps, s, counter, dbuf);
       MX_FOR_EACH_LEN(X)
 #undef X
     }

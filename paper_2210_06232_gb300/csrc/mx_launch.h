@@ -23,10 +23,12 @@ cudaError_t launch_x_r2c(int M, const T* in_e, const T* in_h, cx<T>* out, long r
 template <typename T>
 cudaError_t launch_x_c2r(int M, const cx<T>* in, T* out_e, T* out_h, long rows3, long nrows, const twv<T>* tw,
                          double scale, int bps, cudaStream_t s, unsigned* counter = nullptr);
-// dir = -1 forward, +1 inverse (unnormalised)
+// dir = -1 forward, +1 inverse (unnormalised).  counter set: tiles moved by the tensor-copy engine
+// (where the layout allows); dbuf: two input stages that double as exchange buffers (lengths that are
+// multiples of 16), else one input stage and a separate exchange buffer.
 template <typename T>
 cudaError_t launch_strided(int N, int dir, cx<T>* data, long inner, long outer, const twv<T>* tw, int bps,
-                           cudaStream_t s, unsigned* counter = nullptr);
+                           cudaStream_t s, unsigned* counter = nullptr, bool dbuf = false);
 
 // Spectral pass.  mode: 0 = invariants only, 1 = update only, 2 = update + invariants.
 // coef_kind: 0 = Coef<T> table, 1 = CoefHL table (float only), 2 = direct Coef<T>, 3 = direct CoefHL.

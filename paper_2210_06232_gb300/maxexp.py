@@ -97,6 +97,7 @@ def _load():
         "mx_batch_graph_used": (I, [P, C.POINTER(I)]),
         "mx_batch_destroy": (None, [P]),
         "mx_schedule": (I, [P, C.POINTER(I), I]),
+        "mx_set_schedule": (I, [P, C.POINTER(I), I]),
         "mx_spectral_update_noalloc": (I, [V, V, I, I, I, D3, D3, D, D, I, D, C.POINTER(mx_invariants), V]),
         "mx_profile_read": (I, [P, C.POINTER(D), C.POINTER(LL)]),
         "mx_sync": (I, [P]),
@@ -141,6 +142,7 @@ mx_batch_sync = _lib.mx_batch_sync
 mx_batch_graph_used = _lib.mx_batch_graph_used
 mx_batch_destroy = _lib.mx_batch_destroy
 mx_schedule = _lib.mx_schedule
+mx_set_schedule = _lib.mx_set_schedule
 mx_spectral_update_noalloc = _lib.mx_spectral_update_noalloc
 mx_profile_read = _lib.mx_profile_read
 mx_sync = _lib.mx_sync
@@ -263,13 +265,21 @@ class Solver:
         check(mx_autotune(self._h), "mx_autotune")
 
     SCHEDULE_PASSES = ("x_r2c", "y_fwd", "z_fwd", "z_inv", "y_inv", "x_c2r", "z_fused")
+    SCHEDULE_VARIANTS = ("copy-engine", "register-prefetch", "copy-engine-2stage")
 
     def schedule(self):
-        """{pass: (blocks per SM, 'copy-engine' | 'register-prefetch')} in use for this shape."""
+        """{pass: (blocks per SM, 'copy-engine' | 'register-prefetch' | 'copy-engine-2stage')} in use."""
         arr = (C.c_int * 7)()
         check(mx_schedule(self._h, arr, 7), "mx_schedule")
-        return {p: (v & 15, "copy-engine" if (v >> 4) == 0 else "register-prefetch")
-                for p, v in zip(self.SCHEDULE_PASSES, arr)}
+        return {p: (v & 15, self.SCHEDULE_VARIANTS[min(v >> 4, 2)]) for p, v in zip(self.SCHEDULE_PASSES, arr)}
+
+    def set_schedule(self, sched):
+        """Set the schedules of this shape: {pass: (blocks per SM, variant name)}, every pass given."""
+        arr = (C.c_int * 7)()
+        for i, p in enumerate(self.SCHEDULE_PASSES):
+            bps, name = sched[p]
+            arr[i] = int(bps) + 16 * self.SCHEDULE_VARIANTS.index(name)
+        check(mx_set_schedule(self._h, arr, 7), "mx_set_schedule")
 
     def profile(self, enable=True):
         check(mx_profile(self._h, 1 if enable else 0), "mx_profile")
