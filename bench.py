@@ -176,7 +176,8 @@ def whole_job_value(world, units_per_rank, ms):
 KERNEL_NAMES = {
     "x_r2c": "k_x_r2c_tma (x-direction R2C, six fields)",
     "x_c2r": "k_x_c2r_tma (x-direction C2R, six fields)",
-    "y_fft": "k_fft_strided_tma (y-direction, six components; forward and inverse launches)",
+    "y_fft": "k_fft_strided_tma2 / k_fft_strided_tma (y-direction, six components, two-stage or one-stage "
+             "tensor-copy variant as scheduled; forward and inverse launches)",
     "z_fft": "k_fft_strided (z-direction, six components)",
     "z_fused": "k_z_fused_tma (z forward + exponential update + invariants + z inverse, tensor-copy prefetch)",
     "spectral": "k_spectral_tma (exponential update + invariants)",
