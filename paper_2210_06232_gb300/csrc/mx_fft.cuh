@@ -206,11 +206,16 @@ __host__ __device__ constexpr int tw_len(int N, int E) { return tw_stage_off(N, 
 // NBAR < 0 uses __syncwarp() (each line within one warp), NBAR == 0
 // __syncthreads(), NBAR > 0 the named barrier of this thread's group of NBAR
 // (warp-specialised kernels whose producer warp is busy).
-// SS < 0: rows of -SS values with no padding, row p stored at p ^ ((p >> 3) & 1),
-// which puts rows 8 apart (written together at stride R = 8) on alternate halves
-// of the banks; the buffer is then exactly N * -SS values (N a multiple of 16).
+// SS < 0 (see swz_rows): rows of W values with no padding, row p stored at
+// p ^ ((p >> 3) & K): rows 8 apart, written together at stride R = 8, land on
+// different 128-byte bank lines when K + 1 rows share one (K = 1 for 64-byte
+// rows, 3 for 32-byte rows); the buffer is exactly N * W values (N a multiple
+// of K + 1).
+__host__ __device__ constexpr int swz_rows(int W, int K) { return -(W | (K << 16)); }
 __device__ __forceinline__ int xoff(int p, int SS) {
-  return SS == 1 ? p + (p >> 4) : SS > 0 ? (p + (p >> 3)) * SS : (p ^ ((p >> 3) & 1)) * -SS;
+  return SS == 1  ? p + (p >> 4)
+         : SS > 0 ? (p + (p >> 3)) * SS
+                  : (p ^ ((p >> 3) & ((-SS) >> 16))) * ((-SS) & 0xFFFF);
 }
 // Exchange-buffer length (complex values) of one contiguous line of length n.
 __host__ __device__ constexpr int line_buf(int n) { return n + (n >> 4) + 1; }

@@ -541,12 +541,13 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
 // stage first holds the tile's coefficient-table entries (cp.async, during
 // the forward transforms), then takes the next tile while the update and the
 // inverse transforms run; the results leave through an output stage and a
-// tensor store.  Components are then transformed in pairs, which halves the
-// barriers: the second exchange buffer of the forward transforms is the input
-// stage past the coefficients; the inverse transforms exchange through four
-// buffers in the output stage (idle until their results are written, once the
-// previous store has read it), alternating between two pairs so that an
-// exchange has a single barrier.  Invariants of the updated state are summed per thread in T
+// tensor store.  Components are then transformed in threes (ZTile::TRIP; pairs
+// where the buffers do not fit), which cuts the barriers and shares each
+// twiddle load: the forward transforms exchange through unpadded, row-swizzled
+// buffers at the end of the input stage (past the coefficients) and one right
+// after it; the inverse transforms through six in the output stage (idle until
+// their results are written, once the previous store has read it),
+// alternating between two triplets so that an exchange has a single barrier.  Invariants of the updated state are summed per thread in T
 // over a tile, then per warp in a compensated (Kahan) pair of T in shared
 // memory, converted to FP64 at the end: no FP64 arithmetic in the loop, where
 // an FP64 instruction costs the pipe as much with one active lane as with 32.
@@ -560,6 +561,16 @@ struct ZTile {
   static constexpr int NL = 1;       // components per exchange buffer of this size (pairs: see above)
   static constexpr size_t exch_bytes = (size_t)NL * strided_rows(N) * TX * sizeof(cx<T>);
   static constexpr size_t tw_bytes = (size_t)N * sizeof(twv<T>);
+  // unpadded exchange buffer with swizzled rows (swz_rows): XK + 1 rows of TX values per 128-byte line
+  static constexpr size_t xbuf_bytes = (size_t)N * TX * sizeof(cx<T>);
+  static constexpr int XK = TX * (int)sizeof(cx<T>) >= 128 ? 0 : 128 / (TX * (int)sizeof(cx<T>)) - 1;
+  static constexpr size_t coef_bytes = (size_t)E * NT * 32;  // staged coefficient entries (32 bytes each)
+  // components in threes: the forward transforms exchange through the last two buffers' worth of
+  // the input stage and one more right after it, the inverse ones through six in the output stage
+  static constexpr bool TRIP = XK <= 7 && N % (XK + 1) == 0 && coef_bytes + 2 * xbuf_bytes <= stage_bytes &&
+                               6 * xbuf_bytes <= stage_bytes;
+  static constexpr size_t smem_tma = TRIP ? 2 * stage_bytes + xbuf_bytes + tw_bytes + 16
+                                          : 2 * stage_bytes + tw_bytes + exch_bytes + 16;
   // static shared memory of the kernel: compensated sums and the block reduction
   static constexpr size_t static_bytes = (size_t)2 * 32 * NSUM * sizeof(T) + (size_t)32 * NSUM * sizeof(double) + 128;
   // element (comp c, z, column x) of the stage: box z / ZC, laid out [c][z % ZC][x]
@@ -605,12 +616,16 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
   constexpr int LS = strided_rows(N) * TX;  // exchange buffer of one component (TX lines side by side)
   extern __shared__ __align__(128) unsigned char zsmraw[];
   // [input stage, output stage (TMAP only)][twiddles][exchange buffer][mbarrier]; the stages also
-  // serve as second exchange buffers
+  // serve as second exchange buffers.  Triplets: [input stage][exchange buffer][output stage]
+  // [twiddles][mbarrier]
+  constexpr bool TRIP = TMAP && ZT::TRIP;
   C* stage = reinterpret_cast<C*>(zsmraw);
-  C* ostage = reinterpret_cast<C*>(zsmraw + ZT::stage_bytes);
-  twv<T>* tw = reinterpret_cast<twv<T>*>(zsmraw + (TMAP ? 2 * ZT::stage_bytes : 0));
-  C* sm = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(tw) + ZT::tw_bytes);
-  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(sm) + ZT::exch_bytes);
+  C* ostage = reinterpret_cast<C*>(zsmraw + ZT::stage_bytes + (TRIP ? ZT::xbuf_bytes : 0));
+  twv<T>* tw = reinterpret_cast<twv<T>*>(TMAP ? reinterpret_cast<unsigned char*>(ostage) + ZT::stage_bytes : zsmraw);
+  C* sm = TRIP ? reinterpret_cast<C*>(zsmraw + ZT::stage_bytes)
+               : reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(tw) + ZT::tw_bytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(TRIP ? reinterpret_cast<unsigned char*>(tw) + ZT::tw_bytes
+                                                    : reinterpret_cast<unsigned char*>(sm) + ZT::exch_bytes);
   for (int i = threadIdx.x; i < tw_len(N, E); i += blockDim.x) tw[i] = twg[i];
   const int x = threadIdx.x % TX, t = threadIdx.x / TX;
   const long inner = (long)g.mx * g.ny;  // stride between z planes
@@ -679,7 +694,16 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       }
       cp_async_commit();
     }
-    if constexpr (TMAP && (size_t)E * ZT::NT * sizeof(CoefT) + ZT::exch_bytes <= ZT::stage_bytes) {
+    constexpr int SWZ = swz_rows(TX, ZT::XK);
+    constexpr int LX = N * TX;  // complex values per unpadded exchange buffer
+    if constexpr (TRIP) {
+      static_assert(sizeof(CoefT) == 32, "coefficient entries of 32 bytes");
+      // three components at a time through the input stage's last two buffers' worth and the one
+      // after it (the coefficients fill the start of the stage)
+      C* fb = reinterpret_cast<C*>(zsmraw + ZT::stage_bytes - 2 * ZT::xbuf_bytes);
+#pragma unroll
+      for (int c = 0; c < 6; c += 3) lines_fft<T, N, E, -1, 0, 3>(v + c, fb + x, SWZ, LX, t, tw);
+    } else if constexpr (TMAP && (size_t)E * ZT::NT * sizeof(CoefT) + ZT::exch_bytes <= ZT::stage_bytes) {
       // two components at a time: the second exchange buffer is the input stage past the coefficients
       C* xb2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(stage) + (size_t)E * ZT::NT * sizeof(CoefT));
       const int ls2 = (int)(xb2 - sm);
@@ -744,7 +768,13 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
         zhi[warp][k] = tv;
       }
     }
-    if constexpr (TMAP) {
+    if constexpr (TRIP) {
+      // three components at a time through the output stage: exchanges alternate between two
+      // triplets of buffers there, so that none waits for the readers of the one before it
+#pragma unroll
+      for (int c = 0; c < 6; c += 3)
+        lines_fft<T, N, E, +1, 0, 3, 1, 0, true>(v + c, ostage + x, SWZ, LX, t, tw, ostage + 3 * LX + x);
+    } else if constexpr (TMAP) {
       // two components at a time through the output stage: exchanges alternate between two pairs
       // of buffers there, so that none waits for the readers of the one before it
       static_assert(ZT::exch_bytes <= ZT::stage_bytes, "an exchange buffer fits in the output stage");

@@ -107,8 +107,8 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided_tma(long inner, lo
 }
 
 // Two input stages, each of which, once read, is also the exchange buffer of
-// its tile's transform (rows swizzled instead of padded, so that the exchange
-// fits the stage: N a multiple of 16), and an output stage: two tiles are in
+// its tile's transform (rows swizzled instead of padded, swz_rows, so that the
+// exchange fits the stage: N a multiple of 16), and an output stage: two tiles are in
 // flight per block while one is transformed.  Stage s takes tiles it, it + 2,
 // ... of the block's sequence; its mbarrier completes once per tile.
 template <typename T, int N, int E, int TX>
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided_tma2(long inner, l
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = st[ST::index(t + P * m, x)];
     // the transform's first exchange waits for every read of the stage above
-    line_fft<T, N, E, DIR>(v, st + x, -TX, t, tw);
+    line_fft<T, N, E, DIR>(v, st + x, swz_rows(TX, 1), t, tw);
     if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tile's store has read the output stage
     __syncthreads();                              // and every exchange read of this stage is done
 #pragma unroll

@@ -43,7 +43,7 @@ cudaError_t zf_n(cx<T>* data, const GridParams& g, const void* tab, double t, co
     const CoefT* tb = reinterpret_cast<const CoefT*>(tab);
     cudaError_t err;
     // with the tensor-copy prefetch when the stage fits beside the exchange buffers
-    constexpr size_t smem_tma = 2 * ZT::stage_bytes + ZT::tw_bytes + ZT::exch_bytes + 16;
+    constexpr size_t smem_tma = ZT::smem_tma;
     if constexpr (smem_tma + ZT::static_bytes <= 232448) {  // shared memory of a block on sm_103a
       CUtensorMap m;
       if (pipelined && counter && z_tensor_map<T, N, E, TX>(&m, data, g)) {
