@@ -260,9 +260,11 @@ __host__ __device__ constexpr int line_bar(int P, int wide) { return (P <= 32 &&
 // is even, in which case the caller guarantees that the previous transform
 // also ran with PP on the same sm and sm2 (its last exchange used sm2) or that
 // a barrier has passed since sm was last read.
-template <typename T, int N, int E, int DIR, int NBAR, int NL, int NS = 1, int IX = 0, bool PP = false>
+// CNS > 1: the twiddles of the stage with NS == CNS come from twr (tw_cached),
+// in registers, instead of tw.
+template <typename T, int N, int E, int DIR, int NBAR, int NL, int NS = 1, int IX = 0, bool PP = false, int CNS = 0>
 __device__ __forceinline__ void lines_fft(cx<T> (*v)[E], cx<T>* sm, int SS, int LS, int t, const twv<T>* tw,
-                                          cx<T>* sm2 = nullptr) {
+                                          cx<T>* sm2 = nullptr, const twv<T>* twr = nullptr) {
   if constexpr (NS < N) {
     constexpr int P = N / E;
     constexpr int R = pick_radix(N / NS, E);
@@ -276,7 +278,7 @@ __device__ __forceinline__ void lines_fft(cx<T> (*v)[E], cx<T>* sm, int SS, int 
         constexpr int OFF = tw_stage_off(N, E, NS);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const twv<T> w = tw[OFF + (r - 1) * NS + k];
+          const twv<T> w = NS == CNS ? twr[b * (R - 1) + r - 1] : tw[OFF + (r - 1) * NS + k];
 #pragma unroll
           for (int l = 0; l < NL; ++l) v[l][b + r * B] = twmul<DIR>(v[l][b + r * B], w);
         }
@@ -303,8 +305,26 @@ __device__ __forceinline__ void lines_fft(cx<T> (*v)[E], cx<T>* sm, int SS, int 
       for (int l = 0; l < NL; ++l)
 #pragma unroll
         for (int m = 0; m < E; ++m) v[l][m] = xb[l * LS + xoff(t + P * m, SS)];
-      lines_fft<T, N, E, DIR, NBAR, NL, NS * R, IX + 1, PP>(v, sm, SS, LS, t, tw, sm2);
+      lines_fft<T, N, E, DIR, NBAR, NL, NS * R, IX + 1, PP, CNS>(v, sm, SS, LS, t, tw, sm2, twr);
     }
+  }
+}
+
+// The second stage's radix and the number of its twiddles a thread uses (B (R - 1)).
+__host__ __device__ constexpr int tw_cache_ns(int N, int E) { return pick_radix(N, E) < N ? pick_radix(N, E) : 0; }
+__host__ __device__ constexpr int tw_cache_len(int N, int E) {
+  return tw_cache_ns(N, E) ? (E / pick_radix(N / tw_cache_ns(N, E), E)) * (pick_radix(N / tw_cache_ns(N, E), E) - 1) : 1;
+}
+// Twiddles of the stage NS = tw_cache_ns(N, E) for thread t, in the order lines_fft reads them.
+template <typename T, int N, int E>
+__device__ __forceinline__ void tw_cached(twv<T>* twr, const twv<T>* tw, int t) {
+  constexpr int NS = tw_cache_ns(N, E);
+  if constexpr (NS > 0 && NS < N) {
+    constexpr int P = N / E, R = pick_radix(N / NS, E), B = E / R, OFF = tw_stage_off(N, E, NS);
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 1; r < R; ++r) twr[b * (R - 1) + r - 1] = tw[OFF + (r - 1) * NS + (t + P * b) % NS];
   }
 }
 

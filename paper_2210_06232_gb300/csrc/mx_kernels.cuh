@@ -619,6 +619,8 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
   // serve as second exchange buffers.  Triplets: [input stage][exchange buffer][output stage]
   // [twiddles][mbarrier]
   constexpr bool TRIP = TMAP && ZT::TRIP;
+  constexpr int TWC = TRIP ? tw_cache_ns(N, E) : 0;  // second-stage twiddles kept in registers
+  twv<T> twr[tw_cache_len(N, E)];
   C* stage = reinterpret_cast<C*>(zsmraw);
   C* ostage = reinterpret_cast<C*>(zsmraw + ZT::stage_bytes + (TRIP ? ZT::xbuf_bytes : 0));
   twv<T>* tw = reinterpret_cast<twv<T>*>(TMAP ? reinterpret_cast<unsigned char*>(ostage) + ZT::stage_bytes : zsmraw);
@@ -644,6 +646,7 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       mbar_fence_init();
     }
     __syncthreads();
+    if constexpr (TRIP && TWC > 0) tw_cached<T, N, E>(twr, tw, t);
     if (threadIdx.x == 0 && (long)blockIdx.x < ntiles) z_tile_copy<T, N, E, TX>(tmap, stage, full, blockIdx.x, ntx);
   }
   unsigned it = 0;
@@ -702,7 +705,8 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       // after it (the coefficients fill the start of the stage)
       C* fb = reinterpret_cast<C*>(zsmraw + ZT::stage_bytes - 2 * ZT::xbuf_bytes);
 #pragma unroll
-      for (int c = 0; c < 6; c += 3) lines_fft<T, N, E, -1, 0, 3>(v + c, fb + x, SWZ, LX, t, tw);
+      for (int c = 0; c < 6; c += 3)
+        lines_fft<T, N, E, -1, 0, 3, 1, 0, false, TWC>(v + c, fb + x, SWZ, LX, t, tw, nullptr, twr);
     } else if constexpr (TMAP && (size_t)E * ZT::NT * sizeof(CoefT) + ZT::exch_bytes <= ZT::stage_bytes) {
       // two components at a time: the second exchange buffer is the input stage past the coefficients
       C* xb2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(stage) + (size_t)E * ZT::NT * sizeof(CoefT));
@@ -773,7 +777,7 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       // triplets of buffers there, so that none waits for the readers of the one before it
 #pragma unroll
       for (int c = 0; c < 6; c += 3)
-        lines_fft<T, N, E, +1, 0, 3, 1, 0, true>(v + c, ostage + x, SWZ, LX, t, tw, ostage + 3 * LX + x);
+        lines_fft<T, N, E, +1, 0, 3, 1, 0, true, TWC>(v + c, ostage + x, SWZ, LX, t, tw, ostage + 3 * LX + x, twr);
     } else if constexpr (TMAP) {
       // two components at a time through the output stage: exchanges alternate between two pairs
       // of buffers there, so that none waits for the readers of the one before it
