@@ -605,7 +605,10 @@ __device__ __forceinline__ void z_tile_copy(const void* tmap, cx<T>* stage, uint
                 full);
 }
 
-template <typename T, int N, int E, int TX, typename CoefT, bool INV, bool TMAP>
+// SRC: where the coefficients come from: 0 = the table (tab set), 1 = computed per point in FP64
+// (tab null), 2 = either, decided at run time.  An instantiation without the FP64 path carries no
+// FP64 code, and no call into the FP64 sine's slow path, in its loop.
+template <typename T, int N, int E, int TX, typename CoefT, bool INV, bool TMAP, int SRC>
 __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const GridParams& g, const CoefT* __restrict__ tab,
                                              double tstep, const twv<T>* __restrict__ twg, double* __restrict__ partials,
                                              unsigned* __restrict__ counter, double* __restrict__ record,
@@ -728,20 +731,30 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
         const int mz = signed_index(t + P * m, N);
         const T kz = nuz * (T)mz;
         CoefT q;
-        if (staged) {
+        auto from_stage = [&]() {
           union {
             CoefT c;
             float4 f[NPC];
           } u;
 #pragma unroll
           for (int h = 0; h < NPC; ++h) u.f[h] = cpl[(h * E + m) * ZT::NT + threadIdx.x];
-          q = u.c;
-        } else if (tab) {
-          q = tab[g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz];
-        } else {
+          return u.c;
+        };
+        auto direct = [&]() {
           const double k2 = g.nu[0] * g.nu[0] * (double)col * col + g.nu[1] * g.nu[1] * (double)my * my +
                             g.nu[2] * g.nu[2] * (double)mz * mz;
-          q = coef_direct<T, CoefT>(k2, tstep, g);
+          return coef_direct<T, CoefT>(k2, tstep, g);
+        };
+        if constexpr (SRC == 1) {
+          q = direct();
+        } else if constexpr (SRC == 0 && TMAP) {
+          q = from_stage();  // staged: the table is set and this column is inside the grid
+        } else if constexpr (SRC == 0) {
+          q = tab[g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz];
+        } else {
+          if (staged) q = from_stage();
+          else if (tab) q = tab[g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz];
+          else q = direct();
         }
         C ee[3] = {v[0][m], v[1][m], v[2][m]};
         C hh[3] = {v[3][m], v[4][m], v[5][m]};
@@ -828,12 +841,14 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
   }
 }
 
-template <typename T, int N, int E, int TX, typename CoefT, bool INV>
+// DIRECT: coefficients computed per point (no table); else from the table, which must be set.
+template <typename T, int N, int E, int TX, typename CoefT, bool INV, bool DIRECT>
 __global__ void __launch_bounds__((N / E) * TX, 1)
     k_z_fused_tma(cx<T>* __restrict__ data, GridParams g, const CoefT* __restrict__ tab, double tstep,
                   const twv<T>* __restrict__ twg, double* __restrict__ partials, unsigned* __restrict__ counter,
                   double* __restrict__ record, const __grid_constant__ CUtensorMap tmap) {
-  z_fused_body<T, N, E, TX, CoefT, INV, true>(data, g, tab, tstep, twg, partials, counter, record, &tmap);
+  z_fused_body<T, N, E, TX, CoefT, INV, true, DIRECT ? 1 : 0>(data, g, tab, tstep, twg, partials, counter, record,
+                                                            &tmap);
 }
 
 template <typename T, int N, int E, int TX, typename CoefT, bool INV>
@@ -841,7 +856,7 @@ __global__ void __launch_bounds__((N / E) * TX, 1) k_z_fused(cx<T>* __restrict__
                                                              const CoefT* __restrict__ tab, double tstep,
                                                              const twv<T>* __restrict__ twg, double* __restrict__ partials,
                                                              unsigned* __restrict__ counter, double* __restrict__ record) {
-  z_fused_body<T, N, E, TX, CoefT, INV, false>(data, g, tab, tstep, twg, partials, counter, record, nullptr);
+  z_fused_body<T, N, E, TX, CoefT, INV, false, 2>(data, g, tab, tstep, twg, partials, counter, record, nullptr);
 }
 
 // ------------------------------------------------------ spectral update pass

@@ -47,15 +47,12 @@ cudaError_t zf_n(cx<T>* data, const GridParams& g, const void* tab, double t, co
     if constexpr (smem_tma + ZT::static_bytes <= 232448) {  // shared memory of a block on sm_103a
       CUtensorMap m;
       if (pipelined && counter && z_tensor_map<T, N, E, TX>(&m, data, g)) {
-        if (record) {
-          auto k = k_z_fused_tma<T, N, E, TX, CoefT, true>;
-          if ((err = set_smem(k, smem_tma)) != cudaSuccess) return err;
-          k<<<grid, P * TX, smem_tma, s>>>(data, g, tb, t, tw, partials, counter, record, m);
-        } else {
-          auto k = k_z_fused_tma<T, N, E, TX, CoefT, false>;
-          if ((err = set_smem(k, smem_tma)) != cudaSuccess) return err;
-          k<<<grid, P * TX, smem_tma, s>>>(data, g, tb, t, tw, partials, counter, record, m);
-        }
+        // one instantiation per coefficient source (a table, or FP64 per point), with or without invariants
+        auto k = record ? (tb ? k_z_fused_tma<T, N, E, TX, CoefT, true, false> : k_z_fused_tma<T, N, E, TX, CoefT, true, true>)
+                        : (tb ? k_z_fused_tma<T, N, E, TX, CoefT, false, false>
+                              : k_z_fused_tma<T, N, E, TX, CoefT, false, true>);
+        if ((err = set_smem(k, smem_tma)) != cudaSuccess) return err;
+        k<<<grid, P * TX, smem_tma, s>>>(data, g, tb, t, tw, partials, counter, record, m);
         return cudaGetLastError();
       }
     }
