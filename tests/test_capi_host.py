@@ -73,3 +73,12 @@ def test_footprint_is_host_only_and_scales():
     assert b64 > 18 * 512 ** 3 * 8 * 0.99 and b32 < b64
     with pytest.raises(mx.MaxexpError):
         mx.footprint_bytes((7, 8, 8))
+
+
+def test_schedule_calls_validate_without_gpu():
+    mx = _lib()
+    arr = (C.c_int * 7)(*([4] * 7))
+    assert mx.mx_schedule(None, arr, 7) == mx.MX_E_INVAL
+    assert mx.mx_set_schedule(None, arr, 7) == mx.MX_E_INVAL
+    assert mx.mx_autotune(None) == mx.MX_E_INVAL
+    assert mx.Solver.SCHEDULE_VARIANTS.index("copy-engine-2stage") == 2  # code = bps + 16 * variant
