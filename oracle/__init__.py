@@ -4,11 +4,14 @@ pseudospectral scheme for periodic 3D Maxwell (Wang & Jiang, arXiv 2210.06232).
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
 or run anything in this package.  The product library never calls it, and it
-shares no code with the CUDA path: it uses numpy only (``numpy.fft`` as the
-library FFT primitive, ``numpy.linalg.eigh`` for the brute-force check).
+shares no code with the CUDA path: it uses numpy only (its own mixed-radix
+FFT in ``fft``, ``numpy.linalg.eigh`` for the brute-force check; no library
+transform).
 
 Modules
 -------
+``fft``          The 1D and 3D DFT of Sec. 2.3 by a recursive mixed-radix (2, 3,
+                 5) Cooley-Tukey FFT, other prime factors by the definition.
 ``scheme``       Alg. 1 (initial values) and Alg. 2 (fully discrete scheme) of
                  Sec. 2.4-2.5, in the paper's order and notation: wavenumber
                  vectors a_w, b_w, Psi, the coefficients r1, r2, c11..c33,

@@ -5,14 +5,16 @@ Test infrastructure only (see ``oracle/__init__.py``).
 Arrays are laid out [component][Nz][Ny][Nx] (x fastest), which is the
 paper's vector ordering of Sec. 2.2.  The 3D DFT of the paper,
 F_{N_z} (x) F_{N_y} (x) F_{N_x} with entries exp(-2 pi i j k / N) and the
-inverse carrying 1/N per axis (Sec. 2.3), is ``numpy.fft.fftn`` /
-``numpy.fft.ifftn`` over the three spatial axes (library FFT primitive;
-``tests/test_oracle_pins.py`` checks it against the DFT matrix written
-from the definition).
+inverse carrying 1/N per axis (Sec. 2.3), is the oracle's own mixed-radix
+FFT (``oracle/fft.py``) over the three spatial axes; ``tests/test_oracle_pins.py``
+checks it against the DFT matrix and a naive O(N_S^2) 3D DFT written from the
+definition.
 """
 from __future__ import annotations
 
 import numpy as np
+
+from .fft import fft3, ifft3
 
 
 def wavenumber_vector(n, lo, hi):
@@ -44,12 +46,12 @@ def b_vectors(nxyz, lo, hi):
 
 def forward3(u):
     """Alg. 1 step 4 / eq. (tran0): (F_{Nz} (x) F_{Ny} (x) F_{Nx}) u for each component."""
-    return np.fft.fftn(u, axes=(-3, -2, -1))
+    return fft3(u)
 
 
 def inverse3(uh):
     """Alg. 2 step 5 / eq. (tran1): (F^{-1}_{Nz} (x) F^{-1}_{Ny} (x) F^{-1}_{Nx}) uh."""
-    return np.fft.ifftn(uh, axes=(-3, -2, -1))
+    return ifft3(uh)
 
 
 def coefficients(nxyz, lo, hi, eps, mu, t):

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import bruteforce, closed_form as cf, invariants as inv, scheme
+from oracle import bruteforce, closed_form as cf, fft as offt, invariants as inv, scheme
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")
 
@@ -37,6 +37,56 @@ def test_forward_is_paper_dft_along_each_axis(n):
     Finv = np.conj(F) / n  # (F^{-1})_{jk} = (1/N) exp(2 pi i/N)^{jk}
     np.testing.assert_allclose(Finv @ F, np.eye(n), atol=1e-12)
     np.testing.assert_allclose(scheme.inverse3((F @ u).reshape(1, 1, n)).ravel(), u, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", list(range(1, 41)) + [64, 96, 125, 128, 160, 243, 250])
+def test_oracle_fft_is_dft_matrix(n):
+    """The oracle's mixed-radix FFT against the transform's matrix, forward and inverse, for every
+    length up to 40 (radices 2, 3, 5, their products and the prime lengths finished by the
+    definition) and longer 2/3/5-smooth lengths where a wrong twiddle index or digit order shows."""
+    rng = np.random.default_rng(1000 + n)
+    x = rng.standard_normal((3, n)) + 1j * rng.standard_normal((3, n))
+    F = dft_matrix(n)
+    scale = np.abs(x).max() * n
+    np.testing.assert_allclose(offt.fft(x), x @ F.T, rtol=0, atol=1e-13 * scale)
+    np.testing.assert_allclose(offt.ifft(x), x @ np.conj(F).T / n, rtol=0, atol=1e-13 * scale / n)
+    np.testing.assert_allclose(offt.ifft(offt.fft(x)), x, rtol=0, atol=1e-13 * np.abs(x).max())
+
+
+def _naive_dft3(u, sign):
+    """sum over all N_S points of u_j exp(sign 2 pi i (jx kx/Nx + jy ky/Ny + jz kz/Nz)): the 3D DFT
+    written out with one N_S x N_S exponent matrix (no factorisation into axes)."""
+    nz, ny, nx = u.shape[-3:]
+    jz, jy, jx = (a.ravel() for a in np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij"))
+    ph = (np.outer(jx, jx) / nx + np.outer(jy, jy) / ny + np.outer(jz, jz) / nz)
+    W = np.exp(sign * 2j * np.pi * ph)
+    return (u.reshape(u.shape[:-3] + (-1,)) @ W.T).reshape(u.shape)
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (12, 10, 6), (5, 9, 7)])
+def test_oracle_fft3_is_naive_3d_dft(shape):
+    """forward3/inverse3 against the naive O(N_S^2) 3D DFT at 8^3 and on cuboids with radices 2, 3, 5
+    (and the prime lengths 5, 7 by the definition), [Nz][Ny][Nx] with x fastest."""
+    rng = np.random.default_rng(sum(shape))
+    u = rng.standard_normal((2,) + shape)
+    X = scheme.forward3(u)
+    ref = _naive_dft3(u, -1)
+    np.testing.assert_allclose(X, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    ns = int(np.prod(shape))
+    np.testing.assert_allclose(scheme.inverse3(X), _naive_dft3(X, +1) / ns, rtol=0, atol=1e-12 * np.abs(u).max())
+    # Parseval: sum |u|^2 = (1/N_S) sum |X|^2
+    assert abs(np.sum(np.abs(X) ** 2) / ns - np.sum(u ** 2)) < 1e-12 * np.sum(u ** 2)
+
+
+def test_oracle_fft3_agrees_with_library_fft_at_size():
+    """At sizes where a naive DFT is out of reach, the library transform (numpy.fft) serves as a pin
+    of the oracle's own: 30 x 32 x 48 and a 512-long line."""
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal((48, 32, 30))
+    ref = np.fft.fftn(u)
+    np.testing.assert_allclose(scheme.forward3(u), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    x = rng.standard_normal(512) + 1j * rng.standard_normal(512)
+    np.testing.assert_allclose(offt.fft(x), np.fft.fft(x), rtol=0, atol=1e-12 * np.abs(x).sum())
 
 
 def test_forward_is_kronecker_product_in_x_fastest_order():
