@@ -316,19 +316,26 @@ mx_status mx_profile_read(mx_ctx* ctx, double* ms, long long* launches);
  *              the unnormalised 3D DFT of real fields with column kx = 0
  *              holding the kx = 0 plane in its real part and the kx = nx/2
  *              plane in its imaginary part.
- *  spec_out  : device, same layout; receives R(t) spec_in (may equal
- *              spec_in).  NULL: no update, invariants of spec_in only.
+ *              Must start on a 16-byte boundary.
+ *  spec_out  : device, same layout and alignment; receives R(t) spec_in
+ *              (may equal spec_in).  NULL: no update, invariants of spec_in
+ *              only.
  *  inv_out   : host; receives the invariants of the written spectrum (of
  *              spec_in when spec_out is NULL), t = t, step = 0.  NULL: none.
- *              When given, the call waits for the stream.
+ *              When given, the call waits for the stream, so it cannot be
+ *              made while the stream is being captured (MX_E_INVAL); the
+ *              update alone (inv_out NULL) enqueues only a memset and one
+ *              kernel.
  *  nx..mu, precision : as for mx_create (any even sizes >= 2).
  *  stream    : cudaStream_t or NULL.
  * Device memory: besides spec_in and spec_out the pass uses one static
  * device array of about 40 KB (partial sums of at most 304 blocks, a block
  * counter and one record), present on every device that loads the library.
  * Coefficients are computed per point in FP64 (no table), so the pass is
- * slower than mx_step.  Errors: MX_E_INVAL for bad arguments,
- * MX_E_UNSUPPORTED_N when (nx/2) * ny * nz >= 2^31, MX_E_CUDA otherwise.
+ * slower than mx_step.  Errors: MX_E_INVAL for bad arguments (including a
+ * spectrum pointer that is not 16-byte aligned, checked before anything is
+ * enqueued, and inv_out during a stream capture), MX_E_UNSUPPORTED_N when
+ * (nx/2) * ny * nz >= 2^31, MX_E_CUDA otherwise.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array: calls that overlap on the GPU (concurrent

@@ -8,6 +8,7 @@
 // lives in one file-scope __device__ array of fixed size, which every GPU
 // that loads the library holds until the process exits.
 #include <math.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <mutex>
@@ -64,6 +65,8 @@ extern "C" mx_status mx_spectral_update_noalloc(const void* spec_in, void* spec_
                                                 const double lo[3], const double hi[3], double eps, double mu,
                                                 int precision, double t, mx_invariants* inv_out, void* stream) {
   if (!spec_in || !lo || !hi) return MX_E_INVAL;
+  // the pass moves whole 16-byte pieces (double2 points, float4 point pairs)
+  if ((((uintptr_t)spec_in) | ((uintptr_t)spec_out)) & 15u) return MX_E_INVAL;
   if (nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2) return MX_E_INVAL;
   if (!(eps > 0.0) || !(mu > 0.0) || !isfinite(eps) || !isfinite(mu) || !isfinite(t)) return MX_E_INVAL;
   if (precision != MX_FP64 && precision != MX_FP32) return MX_E_INVAL;
@@ -84,6 +87,10 @@ extern "C" mx_status mx_spectral_update_noalloc(const void* spec_in, void* spec_
   mx::set_material(g, eps, mu);
 
   cudaStream_t s = (cudaStream_t)stream;
+  // reading the invariants back needs a copy into host memory and a wait: neither can be recorded
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return MX_E_CUDA;
+  if (cap != cudaStreamCaptureStatusNone && inv_out) return MX_E_INVAL;
   unsigned char* scratch = nullptr;
   if (scratch_ptr(&scratch) != cudaSuccess) return MX_E_CUDA;
   // the block counter and the wait-timeout flag after it must start at zero

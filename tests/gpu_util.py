@@ -46,6 +46,21 @@ def rel_l2(E, H, Er, Hr):
     return num / max(den, 1e-300)
 
 
+def field_rel_l2(E, H, Er, Hr):
+    """Relative L2 error of each of the six fields (E_x, E_y, E_z, H_x, H_y, H_z) against its reference."""
+    out = []
+    for X, R in ((E, Er), (H, Hr)):
+        for c in range(3):
+            den = np.sqrt(np.sum(np.asarray(R[c]) ** 2))
+            out.append(float(np.sqrt(np.sum((np.asarray(X[c]) - np.asarray(R[c])) ** 2)) / max(den, 1e-300)))
+    return out
+
+
+def max_field_rel_l2(E, H, Er, Hr):
+    """The worst of the six per-field relative L2 errors (the per-field tolerance is on this)."""
+    return max(field_rel_l2(E, H, Er, Hr))
+
+
 def inv_scales(r, eps, mu):
     """Cauchy-Schwarz bounds to normalise invariants that may be ~0."""
     e1, e2 = abs(r["E1"]), abs(r["E2"])

@@ -82,3 +82,15 @@ def test_schedule_calls_validate_without_gpu():
     assert mx.mx_set_schedule(None, arr, 7) == mx.MX_E_INVAL
     assert mx.mx_autotune(None) == mx.MX_E_INVAL
     assert mx.Solver.SCHEDULE_VARIANTS.index("copy-engine-2stage") == 2  # code = bps + 16 * variant
+
+
+def test_noalloc_alignment_checked_before_any_cuda_call():
+    """Spectrum pointers that are not 16-byte aligned are refused by the host-side checks (the
+    values are never dereferenced)."""
+    mx = _lib()
+    lo = (C.c_double * 3)(0, 0, 0)
+    hi = (C.c_double * 3)(1, 1, 1)
+    a, m = C.c_void_p(1 << 20), C.c_void_p((1 << 20) + 8)
+    for p_in, p_out in ((m, a), (a, m), (m, None)):
+        assert mx.mx_spectral_update_noalloc(p_in, p_out, 8, 8, 8, lo, hi, 1.0, 1.0, mx.MX_FP32, 0.1, None,
+                                             None) == mx.MX_E_INVAL

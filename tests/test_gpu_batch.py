@@ -1,12 +1,12 @@
 """Batched form: instances advanced together by one persistent launch agree
 bit for bit with the same instance run alone, agree with a single-context
-solve to round-off, and (FP64) with the oracle."""
+solve to round-off, and match the oracle field by field (FP64 and FP32)."""
 import numpy as np
 import pytest
 
 import synth
 from oracle import scheme
-from tests.gpu_util import inv_diff, inv_scales, rel_l2, solver_mod
+from tests.gpu_util import field_rel_l2, inv_diff, inv_scales, rel_l2, solver_mod
 
 pytestmark = pytest.mark.gpu
 
@@ -95,18 +95,27 @@ def test_batch_alone_equals_in_mix_and_single_context(prec):
             assert inv_diff(ra, rb, sc) < tol
 
 
-def test_batch_fp64_matches_oracle():
-    import torch
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_matches_oracle_per_field(prec):
+    """Every instance of a mixed batch against the oracle (one step of size 9 h), each of the six
+    fields within 1e-12 (FP64) or 1e-5 (FP32) relative L2, invariants of the last record within
+    the same tolerance of the oracle's physical-space values."""
+    from oracle import invariants as oinv
 
     mx = solver_mod()
-    specs = [SPECS[3], SPECS[4], dict(n=(16, 12, 8), eps=1.7, mu=0.6, h=0.043)]
-    b = mx.Batch(specs, mx.MX_FP64)
+    P = mx.MX_FP64 if prec == "fp64" else mx.MX_FP32
+    npdt = np.float64 if prec == "fp64" else np.float32
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    specs = [SPECS[3], SPECS[4], dict(n=(16, 12, 8), eps=1.7, mu=0.6, h=0.043),
+             dict(n=(32, 24, 40), eps=2.5, mu=1.5, h=0.071)]
+    b = mx.Batch(specs, P)
     inits = []
     for i, sp in enumerate(specs):
         g = synth.Grid(sp["n"], sp.get("lo", (0, 0, 0)), sp.get("hi", (TWO_PI,) * 3))
         rng = np.random.default_rng(30 + i)
-        E0, H0 = rng.standard_normal((3,) + g.shape), rng.standard_normal((3,) + g.shape)
-        b.instance(i).load(E0.copy(), H0.copy())
+        E0 = rng.standard_normal((3,) + g.shape).astype(npdt).astype(np.float64)
+        H0 = rng.standard_normal((3,) + g.shape).astype(npdt).astype(np.float64)
+        b.instance(i).load(E0.astype(npdt), H0.astype(npdt))
         inits.append((g, E0, H0))
     b.step(9, 3)
     b.sync()
@@ -115,5 +124,12 @@ def test_batch_fp64_matches_oracle():
         inst = b.instance(i)
         E, H = inst.read_numpy()
         Eo, Ho = scheme.solve(E0, H0, g.lo, g.hi, sp["eps"], sp["mu"], 9 * sp["h"])
-        assert rel_l2(E, H, Eo, Ho) < 1e-12
+        errs = field_rel_l2(E.astype(np.float64), H.astype(np.float64), Eo, Ho)
+        assert max(errs) < tol, (i, errs)
+        inv = inst.invariants()
+        assert len(inv) == 4
+        r0 = oinv.invariants(E0, H0, g.lo, g.hi, sp["eps"], sp["mu"])
+        rn = oinv.invariants(Eo, Ho, g.lo, g.hi, sp["eps"], sp["mu"])
+        sc = inv_scales(r0, sp["eps"], sp["mu"])
+        assert inv_diff(inv[-1], rn, sc) < tol
     b.close()

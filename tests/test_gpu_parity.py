@@ -2,7 +2,9 @@
 
 Tolerances: FP64 path within 1e-12 relative L2 of the oracle, invariants
 within 1e-12 of the oracle's physical-space values and conserved to
-1e-13 (normalised by Cauchy-Schwarz bounds); FP32 path within 1e-5.
+1e-13 (normalised by Cauchy-Schwarz bounds); FP32 path within 1e-5.  On
+random fields (every component non-trivial) the L2 bounds hold for each of
+the six fields separately.
 """
 import numpy as np
 import pytest
@@ -11,7 +13,7 @@ import synth
 from oracle import closed_form as cf
 from oracle import invariants as oinv
 from oracle import scheme
-from tests.gpu_util import inv_diff, inv_scales, rel_l2, run_gpu, solver_mod
+from tests.gpu_util import inv_diff, inv_scales, max_field_rel_l2, rel_l2, run_gpu, solver_mod
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +58,7 @@ def test_parity_random_fields(gi, form, prec):
     else:
         Eo, Ho = scheme.solve(E0, H0, g.lo, g.hi, eps, mu, h * steps)
     tol = 1e-12 if prec == "fp64" else 1e-5
-    assert rel_l2(E, H, Eo, Ho) < tol
+    assert max_field_rel_l2(E, H, Eo, Ho) < tol
     # invariants: first and last record against the oracle's physical-space values
     assert len(inv) == steps + 1
     r0 = oinv.invariants(E0, H0, g.lo, g.hi, eps, mu)
@@ -135,7 +137,7 @@ def test_host_buffers_and_roundtrip(prec):
         assert len(inv) == 1
         E, H, inv = run_gpu(g, E0, H0, 1.3, 0.7, P, F, 0.1, 5, device=False)
         Eo, Ho = scheme.step(E0, H0, g.lo, g.hi, 1.3, 0.7, 0.1, 5)
-        assert rel_l2(E, H, Eo, Ho) < (1e-12 if prec == "fp64" else 1e-5)
+        assert max_field_rel_l2(E, H, Eo, Ho) < (1e-12 if prec == "fp64" else 1e-5)
 
 
 def test_reversibility_and_zero_step():
@@ -183,7 +185,7 @@ def test_fp32_spectral_multichunk_blocks(n):
         s.close()
     E64, H64, i64 = res[mx.MX_FP64]
     E32, H32, i32 = res[mx.MX_FP32]
-    assert rel_l2(E32, H32, E64, H64) < 1e-6
+    assert max_field_rel_l2(E32, H32, E64, H64) < 1e-6
     sc = inv_scales(i64[0], 1.3, 0.8)
     assert max(inv_diff(a, b, sc) for a, b in zip(i32, i64)) < 1e-6
 
@@ -263,7 +265,7 @@ def test_parity_longest_lines(n, form, prec):
         Eo, Ho = scheme.step(E0, H0, g.lo, g.hi, eps, mu, h, steps)
     else:
         Eo, Ho = scheme.solve(E0, H0, g.lo, g.hi, eps, mu, h * steps)
-    assert rel_l2(E, H, Eo, Ho) < (1e-12 if prec == "fp64" else 1e-5)
+    assert max_field_rel_l2(E, H, Eo, Ho) < (1e-12 if prec == "fp64" else 1e-5)
     assert len(inv) == steps + 1
 
 

@@ -80,6 +80,76 @@ def test_noalloc_matches_context_path_two_calls(prec):
         assert _rel(out.cpu().numpy().astype(np.complex128), _packed(Er, Hr)) < tol
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_noalloc_modes_and_in_place(prec):
+    """The other documented modes on the same grid: invariants of the input only (spec_out NULL),
+    the update only (inv_out NULL), and the update in place (spec_out == spec_in)."""
+    import torch
+
+    mx = solver_mod()
+    P = mx.MX_FP64 if prec == "fp64" else mx.MX_FP32
+    cdt = torch.complex128 if prec == "fp64" else torch.complex64
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    g = synth.Grid((24, 20, 16), (0.0, 0.0, 0.0), (2.0, 1.7, 1.3))
+    rng = np.random.default_rng(22)
+    E0, H0 = rng.standard_normal((3,) + g.shape), rng.standard_normal((3,) + g.shape)
+    eps, mu, h = 1.7, 0.6, 0.043
+    lo = (C.c_double * 3)(*g.lo)
+    hi = (C.c_double * 3)(*g.hi)
+    spec0 = torch.tensor(_packed(E0, H0), dtype=cdt, device="cuda")
+
+    # out of place, update and invariants: the result the other modes are compared with
+    ref = torch.empty_like(spec0)
+    inv_ref = mx.mx_invariants()
+    assert mx.mx_spectral_update_noalloc(spec0.data_ptr(), ref.data_ptr(), *g.n, lo, hi, eps, mu, P, h,
+                                         C.byref(inv_ref), None) == mx.MX_OK
+    # invariants of the input only: the invariants are conserved, so they equal the updated state's
+    inv0 = mx.mx_invariants()
+    assert mx.mx_spectral_update_noalloc(spec0.data_ptr(), None, *g.n, lo, hi, eps, mu, P, h,
+                                         C.byref(inv0), None) == mx.MX_OK
+    sc = inv_scales(inv_ref.as_dict(), eps, mu)
+    assert inv_diff(inv0.as_dict(), inv_ref.as_dict(), sc) < tol
+    # update only
+    out = torch.empty_like(spec0)
+    assert mx.mx_spectral_update_noalloc(spec0.data_ptr(), out.data_ptr(), *g.n, lo, hi, eps, mu, P, h,
+                                         None, None) == mx.MX_OK
+    torch.cuda.synchronize()
+    assert _rel(out.cpu().numpy().astype(np.complex128), ref.cpu().numpy().astype(np.complex128)) < tol
+    # in place
+    buf = spec0.clone()
+    inv_ip = mx.mx_invariants()
+    assert mx.mx_spectral_update_noalloc(buf.data_ptr(), buf.data_ptr(), *g.n, lo, hi, eps, mu, P, h,
+                                         C.byref(inv_ip), None) == mx.MX_OK
+    torch.cuda.synchronize()
+    assert _rel(buf.cpu().numpy().astype(np.complex128), ref.cpu().numpy().astype(np.complex128)) < tol
+    assert inv_diff(inv_ip.as_dict(), inv_ref.as_dict(), sc) < tol
+
+
+def test_noalloc_rejects_misaligned_and_capture():
+    """A spectrum view that does not start on a 16-byte boundary is refused before anything is
+    enqueued; so is a request for invariants while the stream is being captured."""
+    import torch
+
+    mx = solver_mod()
+    lo = (C.c_double * 3)(0, 0, 0)
+    hi = (C.c_double * 3)(1, 1, 1)
+    inv = mx.mx_invariants()
+    spec = torch.zeros(6 * 8 * 8 * 4 + 1, dtype=torch.complex64, device="cuda")
+    off = spec[1:]  # 8-byte offset
+    assert mx.mx_spectral_update_noalloc(off.data_ptr(), spec.data_ptr(), 8, 8, 8, lo, hi, 1.0, 1.0, mx.MX_FP32, 0.1,
+                                         C.byref(inv), None) == mx.MX_E_INVAL
+    assert mx.mx_spectral_update_noalloc(spec.data_ptr(), off.data_ptr(), 8, 8, 8, lo, hi, 1.0, 1.0, mx.MX_FP32, 0.1,
+                                         None, None) == mx.MX_E_INVAL
+    # a capture that records nothing of ours: the call with invariants is refused before it enqueues
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        st = mx.mx_spectral_update_noalloc(spec.data_ptr(), spec.data_ptr(), 8, 8, 8, lo, hi, 1.0, 1.0, mx.MX_FP32,
+                                           0.1, C.byref(inv), C.c_void_p(s.cuda_stream))
+        spec.add_(0)  # the capture holds one node of its own
+    assert st == mx.MX_E_INVAL
+
+
 def test_noalloc_rejects_bad_arguments():
     mx = solver_mod()
     lo = (C.c_double * 3)(0, 0, 0)
