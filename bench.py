@@ -246,7 +246,22 @@ def drift(inv):
     return float(max(abs(r["E1"] - e0) for r in inv) / abs(e0))
 
 
-def form_entry(name, grid, precision, form, ms, steps, prof, peak, inv, world):
+# flops per k-point (one of the N_S/2 points of the packed half spectrum) of the exponential update
+# (Apply: k.H, k.E, k x E, k x H and the six updated components) and of the fifteen invariant sums
+UPDATE_FLOPS_PER_K = 116
+INVARIANT_FLOPS_PER_K = 90
+
+
+def step_flops(grid, form):
+    """Algorithmic flops of one step: 2.5 N log2 N per real 3D transform of N = grid^3 points (half the
+    classic 5 N log2 N of a complex one), six fields forward and inverse in the literal form (none in the
+    spectral-resident form), plus the update and the invariant sums at every k-point."""
+    ns = grid ** 3
+    fft = 0.0 if form == 1 else 6 * 2 * 2.5 * ns * np.log2(ns)
+    return fft + (ns / 2) * (UPDATE_FLOPS_PER_K + INVARIANT_FLOPS_PER_K)
+
+
+def form_entry(name, grid, precision, form, ms, steps, prof, peak, inv, world, alu_peak=None):
     ns = grid ** 3
     es = 8 if precision == 0 else 4
     step_ms = ms / steps
@@ -264,6 +279,13 @@ def form_entry(name, grid, precision, form, ms, steps, prof, peak, inv, world):
         "energy_rel_drift": drift(inv),
         "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1]},
     }
+    if alu_peak:
+        fl = step_flops(grid, form)
+        ach = fl / (step_ms / 1e3)
+        e["alu_roofline"] = {"bound": "alu", "pipe": "fp64" if precision == 0 else "fp32",
+                             "algorithmic_flops_per_step": fl, "achieved_flops": ach, "peak_flops": alu_peak,
+                             "peak_source": "measured in this run (mx_fma_peak: FMA chains on every SM, "
+                                            "an FMA counting two flops)", "frac": ach / alu_peak}
     return name, e
 
 
@@ -443,6 +465,64 @@ def cufft_comparison(torch, grid, steps=20, warmup=3):
             "ms_per_step": ms, "steps": steps}
 
 
+def _oracle_worker(task):
+    """One host core: oracle solves (Alg. 1 + Alg. 2, one step each) at grid^3 for about budget_s."""
+    grid, budget_s = task
+    import synth
+    from oracle import scheme
+
+    g = synth.Grid((grid,) * 3)
+    E0, H0 = synth.random_divfree_fields(g, seed=SEED, sigma=min(SIGMA, grid / 4))
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        scheme.solve(E0, H0, g.lo, g.hi, 1.0, 1.0, H * (n + 1), check_imag=False)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return g.npoints * n, n
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_all_cores(budget_s=12.0, grid=64):
+    """The same oracle on every host core at once: one process per core (spawned, one numpy thread
+    each), each solving its own copy of a 64^3 sample; throughput = all points solved / wall time."""
+    import multiprocessing as mp
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_worker, [(16, 0.0)] * cores)  # start-up and imports outside the timed region
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [(grid, budget_s)] * cores)
+        el = time.perf_counter() - t0
+    pts = sum(r[0] for r in res)
+    solves = sum(r[1] for r in res)
+    return {
+        "value": pts / el,
+        "unit": UNIT,
+        "cores": cores,
+        "kind": "oracle",
+        "cpu": cpu_model(),
+        "sample": f"{solves} oracle solves (Alg. 1 + Alg. 2, one step each, numpy FP64) at {grid}^3 spread over "
+                  f"{cores} spawned processes (one per core, one numpy thread each), {el:.1f} s wall",
+    }
+
+
 def cpu_baseline_sample(budget_s=15.0):
     """The FP64 oracle (numpy, as it stands) on the host cores: Alg. 1 + Alg. 2 at 128^3."""
     import synth
@@ -463,6 +543,7 @@ def cpu_baseline_sample(budget_s=15.0):
         "unit": UNIT,
         "cores": 1,
         "kind": "oracle",
+        "cpu": cpu_model(),
         "sample": f"{n} oracle solves (Alg. 1 + Alg. 2, one step each, numpy FP64, single-threaded) "
                   f"at 128^3 with the same spectrum type, {el:.1f} s",
     }
@@ -508,40 +589,58 @@ def e2e_run(torch, mx, grid, steps, stream):
     }
 
 
-def reference_arm(args, rank, world):
-    if rank != 0:
-        return
+def _oracle_solve(task):
+    """One oracle solve (Alg. 1 + Alg. 2, one step of size t) at grid^3; returns its seconds."""
+    grid, t = task
     import synth
     from oracle import scheme
 
-    total = args.steps + args.warmup
-    # size the per-step sample so the whole run stays within a few minutes
-    grid = 16
-    for cand in (128, 96, 64, 48, 32, 16):
-        g = synth.Grid((cand,) * 3)
-        E0, H0 = synth.random_divfree_fields(g, seed=SEED, sigma=min(SIGMA, cand / 4))
-        t0 = time.perf_counter()
-        scheme.solve(E0, H0, g.lo, g.hi, 1.0, 1.0, H, check_imag=False)
-        dt = time.perf_counter() - t0
-        if dt * total < 150.0:
-            grid = cand
-            break
-    for i in range(args.warmup):
-        scheme.solve(E0, H0, g.lo, g.hi, 1.0, 1.0, H * (i + 1), check_imag=False)
+    g = synth.Grid((grid,) * 3)
+    E0, H0 = synth.random_divfree_fields(g, seed=SEED, sigma=min(SIGMA, grid / 4))
     t0 = time.perf_counter()
-    for i in range(args.steps):
-        scheme.solve(E0, H0, g.lo, g.hi, 1.0, 1.0, H * (i + 1), check_imag=False)
-    el = time.perf_counter() - t0
-    value = grid ** 3 * args.steps / el
-    sample = (f"oracle (numpy FP64, single-threaded) Alg. 1 + Alg. 2 solve at {grid}^3 per step "
-              f"(the 512^3 workload's per-step work scaled down to fit the time limit)")
+    scheme.solve(E0, H0, g.lo, g.hi, 1.0, 1.0, t, check_imag=False)
+    return time.perf_counter() - t0
+
+
+def reference_arm(args, rank, world):
+    """The oracle as the reference arm, on every host core: each step is one oracle solve per core
+    (spawned processes, one numpy thread each) of a sample of the 512^3 workload scaled down so that
+    the whole run stays within a few minutes; value = points solved per second of wall time."""
+    if rank != 0:
+        return
+    import multiprocessing as mp
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    total = args.steps + args.warmup
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        grid = 16
+        for cand in (128, 96, 64, 48, 32, 16):
+            dt = max(pool.map(_oracle_solve, [(cand, H)] * cores))
+            if dt * total < 150.0:
+                grid = cand
+                break
+        for i in range(args.warmup):
+            pool.map(_oracle_solve, [(grid, H * (i + 1))] * cores)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            pool.map(_oracle_solve, [(grid, H * (i + 1))] * cores)
+        el = time.perf_counter() - t0
+    value = cores * grid ** 3 * args.steps / el
+    sample = (f"oracle (numpy FP64) Alg. 1 + Alg. 2 solve at {grid}^3 on each of {cores} host cores per step "
+              f"(spawned processes, one numpy thread each; the 512^3 workload's per-step work scaled down to fit "
+              f"the time limit)")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic: seeded random divergence-free fields (host generator)",
-        "config": {"workload": f"oracle sample at {grid}^3 of the 512^3 precision-form workload", "grid": [grid] * 3},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": f"oracle sample at {grid}^3 per core of the 512^3 precision-form workload",
+                   "grid": [grid] * 3},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -600,14 +699,17 @@ def main():
                          inv, world)
     forms[name] = e
 
+    alu = None
     if not args.no_secondary:
+        alu = {"fp64_fma_flops": mx.fma_peak(mx.MX_FP64), "fp32_fma_flops": mx.fma_peak(mx.MX_FP32)}
         plan = [("fp64_literal", mx.MX_FP64, mx.MX_FORM_LITERAL, min(args.steps, 10)),
                 ("spectral_resident_fp32", mx.MX_FP32, mx.MX_FORM_SPECTRAL, args.steps),
                 ("spectral_resident_fp64", mx.MX_FP64, mx.MX_FORM_SPECTRAL, min(args.steps, 50))]
         for nm, p, f, k in plan:
             _, ms2, prof2, _, inv2 = run_form(torch, mx, grid, p, f, k, 3, stream, dist)
             ms2 = max_over_ranks(torch, dist, ms2)
-            forms[nm] = form_entry(nm, grid, p, f, ms2, k, prof2, peak, inv2, world)[1]
+            forms[nm] = form_entry(nm, grid, p, f, ms2, k, prof2, peak, inv2, world,
+                                   alu_peak=alu["fp64_fma_flops"] if p == mx.MX_FP64 else None)[1]
 
     e2e = e2e_run(torch, mx, grid, args.steps, stream)
     batched = None if args.no_secondary else batch_run(torch, mx, peak, min(args.steps, 100), args.warmup, stream)
@@ -616,6 +718,7 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline_sample()
+        cpu["all_cores"] = cpu_baseline_all_cores()
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -663,6 +766,7 @@ def main():
         "batched": batched,
         "serve": serve,
         "comparison": comparison,
+        "alu_peaks": alu,
     }
     print(json.dumps(out), flush=True)
     if dist is not None:

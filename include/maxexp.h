@@ -345,6 +345,36 @@ mx_status mx_spectral_update_noalloc(const void* spec_in, void* spec_out, int nx
                                      const double hi[3], double eps, double mu, int precision, double t,
                                      mx_invariants* inv_out, void* stream);
 
+/*
+ * Failure injection for tests (no counterpart in the paper; the library's
+ * error paths are exercised on the host, without a GPU fault).
+ *
+ * mx_debug_fail_alloc(k), k >= 0: the k-th device or pinned-host allocation
+ * the library makes from now on (0 = the next one, counted across all
+ * contexts, batches and servers of the process) fails once, as if the
+ * memory were exhausted; the caller sees MX_E_NOMEM with everything it had
+ * allocated released.  k < 0 disarms.  Process-wide; not for production use.
+ *
+ * mx_debug_wait_limit(ctx, tries): the waits of the context's fused z pass
+ * for its tensor-copied tiles give up after `tries` tries (0: at once)
+ * instead of the default bound; tries < 0 restores the default.  A wait
+ * that gives up makes its block leave the pass (after the copy it issued
+ * has landed) and latches MX_E_TIMEOUT, which mx_sync and every later call
+ * on the context return.  Lets a test reach the timeout path without a
+ * fault or a hang.
+ */
+mx_status mx_debug_fail_alloc(long long k);
+mx_status mx_debug_wait_limit(mx_ctx* ctx, long long tries);
+
+/*
+ * Arithmetic peak of the current device (no counterpart in the paper: the
+ * denominator of the ALU rooflines of the FP64 forms): FMA throughput of
+ * the FP64 (precision MX_FP64) or FP32 pipe in flop/s (an FMA counts two),
+ * best of five timed launches of independent FMA chains on every SM.
+ * Allocates and frees a small output buffer; waits for the device.
+ */
+mx_status mx_fma_peak(int precision, double* flops_per_s);
+
 /* Current time and step count of the context. */
 mx_status mx_time(mx_ctx* ctx, double* t, long long* step);
 

@@ -116,11 +116,11 @@ mx_status mx_batch_create(mx_batch** out, const mx_instance_desc* inst, int n, i
   if (chunks >= (1ULL << 31) || q >= (1ULL << 31)) return bail(MX_E_UNSUPPORTED_N);
   b->total_chunks = (unsigned)chunks;
   b->total_q = (unsigned)q;
-  if (cudaMallocHost(&b->h_inst, sizeof(mx::BInst) * n) != cudaSuccess) return bail(MX_E_NOMEM);
-  if (cudaMalloc(&b->d_inst, sizeof(mx::BInst) * n) != cudaSuccess) return bail(MX_E_NOMEM);
-  if (cudaMalloc(&b->cpart, (size_t)b->total_chunks * mx::BT_CWARPS * mx::NSUM * sizeof(double)) != cudaSuccess)
+  if (mx::host_alloc_pinned((void**)&b->h_inst, sizeof(mx::BInst) * n) != cudaSuccess) return bail(MX_E_NOMEM);
+  if (mx::dev_alloc((void**)&b->d_inst, sizeof(mx::BInst) * n) != cudaSuccess) return bail(MX_E_NOMEM);
+  if (mx::dev_alloc((void**)&b->cpart, (size_t)b->total_chunks * mx::BT_CWARPS * mx::NSUM * sizeof(double)) != cudaSuccess)
     return bail(MX_E_NOMEM);
-  if (cudaMalloc(&b->bar, 64) != cudaSuccess) return bail(MX_E_NOMEM);
+  if (mx::dev_alloc((void**)&b->bar, 64) != cudaSuccess) return bail(MX_E_NOMEM);
   if (cudaMemset(b->bar, 0, 64) != cudaSuccess) return bail(MX_E_CUDA);
   // descriptors that do not change between calls
   unsigned c0 = 0, q0 = 0, s0 = 0;
@@ -145,7 +145,7 @@ mx_status mx_batch_create(mx_batch** out, const mx_instance_desc* inst, int n, i
     s0 += d.nseg;
   }
   b->total_segs = s0;
-  if (cudaMalloc(&b->segpart, (size_t)2 * b->total_segs * mx::NSUM * sizeof(double)) != cudaSuccess)
+  if (mx::dev_alloc((void**)&b->segpart, (size_t)2 * b->total_segs * mx::NSUM * sizeof(double)) != cudaSuccess)
     return bail(MX_E_NOMEM);
   // co-resident grid for the cooperative launch
   const void* kern = precision == MX_FP64 ? batch_kernel<double>() : batch_kernel<float>();

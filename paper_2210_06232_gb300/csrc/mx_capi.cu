@@ -14,6 +14,36 @@
 
 using mx::GridParams;
 
+#include <atomic>
+
+namespace mx {
+
+// Allocation fault injection (mx_debug_fail_alloc): when g_fail_at >= 0, the allocation with that
+// index (counted from the arming call) fails once with cudaErrorMemoryAllocation.
+static std::atomic<long long> g_fail_at{-1};
+static std::atomic<long long> g_alloc_index{0};
+
+static bool injected_failure() {
+  if (g_fail_at.load(std::memory_order_relaxed) < 0) return false;
+  const long long i = g_alloc_index.fetch_add(1);
+  long long k = i;
+  return g_fail_at.compare_exchange_strong(k, -1);  // one-shot
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_alloc_pinned(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  return cudaMallocHost(p, bytes);
+}
+
+}  // namespace mx
+
 #include "mx_ctx.h"
 
 namespace {
@@ -123,13 +153,13 @@ cudaError_t upload_twiddles(mx_ctx* c, int axis, int n, void** dst) {
   re.resize(n, 1.0);
   im.resize(n, 0.0);
   if (c->prec == MX_FP64) {
-    cudaError_t e = cudaMalloc(dst, (size_t)n * sizeof(double2));
+    cudaError_t e = mx::dev_alloc(dst, (size_t)n * sizeof(double2));
     if (e != cudaSuccess) return e;
     std::vector<double2> h(n);
     for (int j = 0; j < n; ++j) h[j] = make_double2(re[j], im[j]);
     return cudaMemcpy(*dst, h.data(), n * sizeof(double2), cudaMemcpyHostToDevice);
   }
-  cudaError_t e = cudaMalloc(dst, (size_t)n * sizeof(float4));
+  cudaError_t e = mx::dev_alloc(dst, (size_t)n * sizeof(float4));
   if (e != cudaSuccess) return e;
   std::vector<float4> h(n);
   for (int j = 0; j < n; ++j) {
@@ -176,7 +206,7 @@ mx_status mx_ensure_records(mx_ctx* c, long long more) {
   if (c->rec_n + more <= c->rec_cap) return MX_OK;
   long long cap = std::max<long long>(c->rec_n + more, std::max<long long>(64, 2 * c->rec_cap));
   double* nr = nullptr;
-  MX_CHECK(c, cudaMalloc(&nr, (size_t)cap * REC_STRIDE * sizeof(double)));
+  MX_CHECK(c, mx::dev_alloc((void**)&nr, (size_t)cap * REC_STRIDE * sizeof(double)));
   if (c->rec && c->rec_n)
     MX_CHECK(c, cudaMemcpyAsync(nr, c->rec, (size_t)c->rec_n * REC_STRIDE * sizeof(double), cudaMemcpyDeviceToDevice,
                                 c->stream));
@@ -646,14 +676,14 @@ mx_status mx_create(mx_ctx** out, int nx, int ny, int nz, const double lo[3], co
     return s;
   };
   const size_t field_bytes = (size_t)6 * c->ns * c->es;
-  if (cudaMalloc(&c->phys, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
-  if (cudaMalloc(&c->spec, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
-  if (form == MX_FORM_SPECTRAL && cudaMalloc(&c->spec0, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
-  if (c->table && cudaMalloc(&c->tab, (size_t)c->nq * 32) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (mx::dev_alloc(&c->phys, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (mx::dev_alloc(&c->spec, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (form == MX_FORM_SPECTRAL && mx::dev_alloc(&c->spec0, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (c->table && mx::dev_alloc(&c->tab, (size_t)c->nq * 32) != cudaSuccess) return fail(MX_E_NOMEM);
   // partial sums for up to 2 blocks per SM of any pass that reduces invariants
   c->pblocks = std::max(c->sblocks, 2 * mx::num_sms());
-  if (cudaMalloc(&c->partials, (size_t)c->pblocks * mx::NSUM * sizeof(double)) != cudaSuccess) return fail(MX_E_NOMEM);
-  if (cudaMalloc(&c->counter, 64) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (mx::dev_alloc((void**)&c->partials, (size_t)c->pblocks * mx::NSUM * sizeof(double)) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (mx::dev_alloc((void**)&c->counter, 64) != cudaSuccess) return fail(MX_E_NOMEM);
   if (cudaMemset(c->counter, 0, 64) != cudaSuccess) return fail(MX_E_CUDA);
   if (upload_twiddles(c, 0, nx, &c->twx) != cudaSuccess) return fail(MX_E_NOMEM);
   if (upload_twiddles(c, 1, ny, &c->twy) != cudaSuccess) return fail(MX_E_NOMEM);
@@ -799,6 +829,22 @@ mx_status mx_time(mx_ctx* c, double* t, long long* step) {
   if (!c) return MX_E_INVAL;
   if (t) *t = c->t;
   if (step) *step = c->step;
+  return MX_OK;
+}
+
+mx_status mx_debug_fail_alloc(long long k) {
+  if (k < 0) {
+    mx::g_fail_at.store(-1);
+    return MX_OK;
+  }
+  mx::g_alloc_index.store(0);
+  mx::g_fail_at.store(k);
+  return MX_OK;
+}
+
+mx_status mx_debug_wait_limit(mx_ctx* c, long long tries) {
+  if (!c) return MX_E_INVAL;
+  c->g.wait_tries = (tries < 0 || tries > (long long)mx::MBAR_TRIES) ? mx::MBAR_TRIES : (unsigned)tries;
   return MX_OK;
 }
 

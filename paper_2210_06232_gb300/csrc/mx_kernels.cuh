@@ -32,6 +32,9 @@ struct GridParams {
   double c;             // 1 / sqrt(eps mu)
   double zh, ze;        // sqrt(eps / mu), sqrt(mu / eps)
   float nuf[3], epsf, muf;  // FP32 copies for the FP32 kernels (no conversion on the FP64 pipe)
+  // tries of the fused z pass's waits for its tiles (MBAR_TRIES unless a test lowers it to make
+  // them give up; the wait for a copy still in flight when a block leaves keeps the full bound)
+  unsigned wait_tries = 1u << 24;
 };
 // Material constants of a grid (host side; after nu is set).
 inline void set_material(GridParams& g, double eps, double mu) {
@@ -662,7 +665,7 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
     C* base = data + (long)y * g.mx + col;
     C v[6][E];
     if constexpr (TMAP) {
-      const bool lost = !mbar_wait_bounded(full, it & 1u);
+      const bool lost = !mbar_wait_tries(full, it & 1u, g.wait_tries);
       if (__syncthreads_or(lost)) {
         if (lost) atomicExch(counter + 1, 1u);
         break;

@@ -13,6 +13,11 @@ bool fft_len_supported(int n);
 // Number of SMs of the current device (cached per process).
 int num_sms();
 
+// Every device (and pinned host) allocation of the library goes through these, so that a test
+// can make the k-th one fail (mx_debug_fail_alloc) and check the callers' cleanup paths.
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t host_alloc_pinned(void** p, size_t bytes);
+
 // Twiddle tables: twv<T> entries exp(-2 pi i j / n) (FP32: hi + lo pairs).
 // bps: persistent grid of bps blocks per SM; 0 = one block per tile.
 // counter: the context's block counter (counter[1] = wait-timeout flag); with

@@ -24,11 +24,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false when the limit was reached
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 24); ++i)
+// Tries of a bounded wait (each try_wait suspends for a system-dependent time limit): far
+// more than any copy in flight needs, so that a wait that gives up signals a fault.
+constexpr uint32_t MBAR_TRIES = 1u << 24;
+// bounded wait of at most `tries` tries: false when the limit was reached
+__device__ __forceinline__ bool mbar_wait_tries(uint64_t* bar, uint32_t parity, uint32_t tries) {
+  for (uint32_t i = 0; i < tries; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_tries(bar, parity, MBAR_TRIES);
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(

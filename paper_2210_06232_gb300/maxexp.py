@@ -100,6 +100,9 @@ def _load():
         "mx_set_schedule": (I, [P, C.POINTER(I), I]),
         "mx_spectral_update_noalloc": (I, [V, V, I, I, I, D3, D3, D, D, I, D, C.POINTER(mx_invariants), V]),
         "mx_profile_read": (I, [P, C.POINTER(D), C.POINTER(LL)]),
+        "mx_debug_fail_alloc": (I, [LL]),
+        "mx_debug_wait_limit": (I, [P, LL]),
+        "mx_fma_peak": (I, [I, C.POINTER(D)]),
         "mx_sync": (I, [P]),
         "mx_strerror": (C.c_char_p, [I]),
         "mx_destroy": (None, [P]),
@@ -145,6 +148,16 @@ mx_schedule = _lib.mx_schedule
 mx_set_schedule = _lib.mx_set_schedule
 mx_spectral_update_noalloc = _lib.mx_spectral_update_noalloc
 mx_profile_read = _lib.mx_profile_read
+mx_debug_fail_alloc = _lib.mx_debug_fail_alloc
+mx_debug_wait_limit = _lib.mx_debug_wait_limit
+mx_fma_peak = _lib.mx_fma_peak
+
+
+def fma_peak(precision):
+    """Measured FMA throughput (flop/s, an FMA counting two) of the FP64 or FP32 pipe."""
+    v = C.c_double(0)
+    check(mx_fma_peak(int(precision), C.byref(v)), "mx_fma_peak")
+    return v.value
 mx_sync = _lib.mx_sync
 mx_strerror = _lib.mx_strerror
 mx_destroy = _lib.mx_destroy

@@ -94,3 +94,12 @@ def test_noalloc_alignment_checked_before_any_cuda_call():
     for p_in, p_out in ((m, a), (a, m), (m, None)):
         assert mx.mx_spectral_update_noalloc(p_in, p_out, 8, 8, 8, lo, hi, 1.0, 1.0, mx.MX_FP32, 0.1, None,
                                              None) == mx.MX_E_INVAL
+
+
+def test_debug_calls_validate_without_gpu():
+    """The failure-injection calls: arming and disarming the allocation fault needs no device; the
+    wait limit needs a context."""
+    mx = _lib()
+    assert mx.mx_debug_fail_alloc(5) == mx.MX_OK
+    assert mx.mx_debug_fail_alloc(-1) == mx.MX_OK
+    assert mx.mx_debug_wait_limit(None, 0) == mx.MX_E_INVAL

@@ -3,9 +3,9 @@ sums -> z inverse in one kernel) at every line length the library dispatches to 
 the FP64 oracle's literal stepping (Alg. 1 + Alg. 2 with t_end = h, repeated).
 
 FP64 has a fused plan for powers of two (2 .. 512), FP32 also for 3 * 2^a (6 .. 384); the
-z length is the only long axis, so the oracle stays cheap.  The x extent 36 (18 complex
-columns, rows of 144 or 288 bytes: the tensor-copy variant applies) leaves a ragged last
-tile for every tile width, and white noise (not divergence
+z length is the only long axis, so the oracle stays cheap.  The x extent (20 in FP32, 10 in
+FP64: 10 or 5 complex columns, rows of 80 bytes, a multiple of 16, so the tensor-copy variant
+applies) leaves a ragged last tile for every tile width, and white noise (not divergence
 free, every wavenumber populated, Nyquist planes included) exercises every coefficient.
 Each test checks, through the context's kernel profile, that the fused kernel ran, then
 compares each of the six fields (FP64 within 1e-12, FP32 within 1e-5 relative L2) and the
@@ -52,7 +52,7 @@ def test_fused_z_length_matches_oracle(prec, nz):
     mx = solver_mod()
     P = mx.MX_FP64 if prec == "fp64" else mx.MX_FP32
     ny = 6 if nz >= 256 else 8
-    g = synth.Grid((36, ny, nz), (0.0, 0.0, 0.0), (2.0, 3.0, 2.5))
+    g = synth.Grid((10 if prec == "fp64" else 20, ny, nz), (0.0, 0.0, 0.0), (2.0, 3.0, 2.5))
     rng = np.random.default_rng(1000 + nz)
     E0, H0 = rng.standard_normal((3,) + g.shape), rng.standard_normal((3,) + g.shape)
     eps, mu, h, steps = 1.6, 0.7, 0.031, 4

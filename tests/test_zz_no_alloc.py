@@ -156,7 +156,7 @@ def test_noalloc_rejects_bad_arguments():
     hi = (C.c_double * 3)(1, 1, 1)
     inv = mx.mx_invariants()
     assert mx.mx_spectral_update_noalloc(None, None, 8, 8, 8, lo, hi, 1.0, 1.0, 0, 0.1, C.byref(inv), None) == mx.MX_E_INVAL
-    dummy = C.c_void_p(1)  # never dereferenced: validation fails first
+    dummy = C.c_void_p(1 << 20)  # 16-byte aligned, never dereferenced: validation fails first
     assert mx.mx_spectral_update_noalloc(dummy, dummy, 7, 8, 8, lo, hi, 1.0, 1.0, 0, 0.1, C.byref(inv), None) == mx.MX_E_INVAL
     assert mx.mx_spectral_update_noalloc(dummy, dummy, 8, 8, 8, lo, hi, -1.0, 1.0, 0, 0.1, C.byref(inv), None) == mx.MX_E_INVAL
     assert mx.mx_spectral_update_noalloc(dummy, dummy, 8, 8, 8, lo, hi, 1.0, 1.0, 0, float("inf"), C.byref(inv), None) == mx.MX_E_INVAL
