@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--grid", type=int, default=512, help="cubic grid size (default 512)")
     ap.add_argument("--no-secondary", action="store_true", help="skip the FP64 and literal-form lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    ap.add_argument("--only", choices=["dft8"], default=None,
+                    help="dft8: only the tensor-core DFT-as-GEMM evaluation (one JSON line; for profiling)")
     return ap.parse_args()
 
 
@@ -523,6 +525,45 @@ def cpu_baseline_all_cores(budget_s=12.0, grid=64):
     }
 
 
+def dft_gemm_eval(torch, mx, tiles=None, reps=64):
+    """Tensor-core DFT-as-GEMM against the FMA radix-8 stage (mx_dft8_stage_eval): `reps` stages of
+    tiles of 128 8-point vectors held on chip (time = the stage's arithmetic and data movement).
+    Error: relative L2 against the same stages in FP64 on the first tile."""
+    import ctypes as C
+
+    tiles = tiles or 8 * torch.cuda.get_device_properties(0).multi_processor_count
+    rng = np.random.default_rng(8)
+    x = (rng.standard_normal((tiles * 128, 8)) + 1j * rng.standard_normal((tiles * 128, 8))).astype(np.complex64)
+    xin = torch.tensor(x, device="cuda")
+    out = torch.empty_like(xin)
+    k = np.arange(8)
+    a = -2.0 * np.pi * (k + 1) / 64.0
+    w = ((np.cos(a) / np.sqrt(8)).astype(np.float32).astype(np.float64) +
+         1j * (np.sin(a) / np.sqrt(8)).astype(np.float32).astype(np.float64))
+    F = np.exp(-2j * np.pi * np.outer(k, k) / 8)
+    ref = x[:128].astype(np.complex128)
+    for _ in range(reps):
+        ref = (ref * w) @ F.T
+    res = {}
+    names = {0: "fma-butterfly", 1: "tcgen05-tf32x1", 3: "tcgen05-tf32x3", 6: "tcgen05-tf32x6"}
+    for v in (0, 1, 3, 6):
+        best = None
+        for _ in range(3):
+            ms = C.c_double(0)
+            mx.check(mx.mx_dft8_stage_eval(v, xin.data_ptr(), out.data_ptr(), tiles, reps, C.byref(ms)),
+                     "mx_dft8_stage_eval")
+            best = ms.value if best is None else min(best, ms.value)
+        y = out[:128].cpu().numpy().astype(np.complex128)
+        dft8s = tiles * 128 * reps
+        res[names[v]] = {"ms": best, "ns_per_dft8_stage": best * 1e6 / dft8s,
+                         "rel_l2_vs_fp64": float(np.linalg.norm(y - ref) / np.linalg.norm(ref)),
+                         "mma_tflops": (2.0 * 16 * 16 * v * dft8s / (best * 1e-3) / 1e12) if v else None}
+    res["what"] = (f"{reps} radix-8 stages (twiddle + 8-point DFT) of {tiles} tiles x 128 vectors; tensor-core "
+                   "variants: 128x16x16 kind::tf32 MMAs with 1/3/6 products of TF32-split operands, result in "
+                   "tensor memory")
+    return res
+
+
 def cpu_baseline_sample(budget_s=15.0):
     """The FP64 oracle (numpy, as it stands) on the host cores: Alg. 1 + Alg. 2 at 128^3."""
     import synth
@@ -659,6 +700,9 @@ def main():
     from paper_2210_06232_gb300 import maxexp as mx
 
     torch.cuda.set_device(local)
+    if args.only == "dft8":
+        print(json.dumps({"dft_as_gemm_stage": dft_gemm_eval(torch, mx, tiles=2 * 152, reps=64)}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as td
@@ -713,7 +757,8 @@ def main():
 
     e2e = e2e_run(torch, mx, grid, args.steps, stream)
     batched = None if args.no_secondary else batch_run(torch, mx, peak, min(args.steps, 100), args.warmup, stream)
-    comparison = None if args.no_secondary else {"cufft_transforms": cufft_comparison(torch, grid)}
+    comparison = None if args.no_secondary else {"cufft_transforms": cufft_comparison(torch, grid),
+                                                 "dft_as_gemm_stage": dft_gemm_eval(torch, mx)}
     serve = None if (args.no_secondary or rank != 0) else serve_run(torch, mx)
     cpu = None
     if rank == 0 and not args.no_cpu:

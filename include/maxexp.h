@@ -375,6 +375,25 @@ mx_status mx_debug_wait_limit(mx_ctx* ctx, long long tries);
  */
 mx_status mx_fma_peak(int precision, double* flops_per_s);
 
+/*
+ * DFT-as-GEMM evaluation (a measurement, not a step of the method; the
+ * paper's cost model, Sec. 2.5, puts the time in the transforms): applies
+ * `reps` radix-8 stages (twiddle by fixed unit-modulus / sqrt(8) factors,
+ * then an 8-point DFT, exp(-2 pi i / 8) kernel) to tiles of 128 independent
+ * 8-point vectors held on chip, and reports the kernel time.
+ *  variant 0 : FMA pipe, the register butterfly of the line FFTs.
+ *  variant 1, 3, 6 : tensor cores (tcgen05.mma, kind::tf32, 128 x 16 x 16
+ *            per tile, result in tensor memory) with 1, 3 or 6 products of
+ *            TF32-split operands (1: TF32 accuracy; 6: about FP32's).
+ *  in, out : device, [tiles * 128][8] complex FP32 (interleaved), 16-byte
+ *            aligned; caller-owned.
+ *  ms      : host; kernel time from CUDA events on the legacy stream.
+ * Allocates and frees a small constant buffer; waits for the device.
+ * Errors: MX_E_INVAL (arguments), MX_E_TIMEOUT (a wait for the tensor core
+ * gave up), MX_E_CUDA.
+ */
+mx_status mx_dft8_stage_eval(int variant, const void* in, void* out, long long tiles, int reps, double* ms);
+
 /* Current time and step count of the context. */
 mx_status mx_time(mx_ctx* ctx, double* t, long long* step);
 

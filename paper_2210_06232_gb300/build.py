@@ -20,7 +20,7 @@ LIB = os.path.join(LIBDIR, "libmaxexp.so")
 # translation units compiled in parallel (the large kernel families are split across several)
 SOURCES = ["mx_capi.cu", "mx_spectral.cu", "mx_fft_f32.cu", "mx_fft_f32s.cu", "mx_fft_f64.cu", "mx_gen.cu",
            "mx_noalloc.cu", "mx_batch.cu", "mx_server.cu", "mx_zfused.cu", "mx_zfused_f32a.cu", "mx_zfused_f32b.cu",
-           "mx_zfused_f32c.cu", "mx_zfused_f32d.cu", "mx_zfused_f64.cu", "mx_probe.cu"]
+           "mx_zfused_f32c.cu", "mx_zfused_f32d.cu", "mx_zfused_f64.cu", "mx_probe.cu", "mx_dft_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--use_fast_math=false",
          "-I", os.path.join(ROOT, "include")]

@@ -143,7 +143,8 @@ void axis_twiddles(int axis, int n, bool fp64, std::vector<double>& re, std::vec
   }
 }
 
-// FP64: double2 per entry.  FP32: float4 (hi.x, hi.y, lo.x, lo.y) with value = hi + lo.
+// FP64: double2 per entry.  FP32: float4 (hi.x, hi.y, lo.x, lo.y) with value = hi + lo, except the
+// fused z pass's lifting constants.
 cudaError_t upload_twiddles(mx_ctx* c, int axis, int n, void** dst) {
   std::vector<double> re, im;
   int zf_off = 0;
@@ -162,7 +163,18 @@ cudaError_t upload_twiddles(mx_ctx* c, int axis, int n, void** dst) {
   cudaError_t e = mx::dev_alloc(dst, (size_t)n * sizeof(float4));
   if (e != cudaSuccess) return e;
   std::vector<float4> h(n);
+  // the fused z pass's entries (from twz_zf on) are lifting constants (p, u, s, 0) of the rotation by
+  // the twiddle's angle a: s = -1 when |a| > pi/2 (a rotation by a -+ pi of the negated value),
+  // p = -tan(a'/2), u = sin a' for the remaining angle a' (mx_fft.cuh, lines_fft_lf)
+  const int lift_from = axis == 2 ? c->twz_zf : n;
   for (int j = 0; j < n; ++j) {
+    if (j >= lift_from && (int)re.size() > lift_from) {
+      double a = atan2(im[j], re[j]), sg = 1.0;
+      if (a > M_PI / 2) a -= M_PI, sg = -1.0;
+      else if (a < -M_PI / 2) a += M_PI, sg = -1.0;
+      h[j] = make_float4((float)(-tan(0.5 * a)), (float)sin(a), (float)sg, 0.f);
+      continue;
+    }
     const float rh = (float)re[j], ih = (float)im[j];
     h[j] = make_float4(rh, ih, (float)(re[j] - (double)rh), (float)(im[j] - (double)ih));
   }

@@ -333,4 +333,213 @@ __device__ __forceinline__ void line_fft(cx<T>* v, cx<T>* sm, int SS, int t, con
   lines_fft<T, N, E, DIR, NBAR, 1>(reinterpret_cast<cx<T>(*)[E]>(v), sm, SS, 0, t, tw);
 }
 
+// ------------------------------------------------- exactly invertible FP32 pair (lifting)
+//
+// For a forward transform, a per-frequency map and an inverse transform applied again and again
+// (the literal form's z pass), FP32 twiddles rounded once bias every step the same way: the
+// inverse does not undo the forward exactly.  This pair removes the bias without double-single
+// constants.  Every rotation of the forward transform is three shears (lifting):
+//   x1 = x + p y,  y1 = y + u x1,  x2 = x1 + p y1   (p = -tan(a/2), u = sin a: rotation by a)
+// which the inverse undoes exactly by the same shears in reverse order with opposite signs, for
+// whatever rounded p and u; rotations with |a| > pi/2 are a rotation by a -+ pi of the negated
+// input (the sign s is exact).  The inverse transform is the forward's mirror: its stages run in
+// reverse order, each undoing the forward stage's butterflies (their inverses up to a power of
+// two: radix 2, 4 and 8 are exact; radix 3 and 5 keep double-single constants) and then its
+// twiddles, and every exchange undoes the forward exchange.  So inverse(forward(x)) = N x up to
+// arithmetic rounding, and n steps of inverse . update . forward equal inverse . update^n .
+// forward: the rounding of the constants does not accumulate.
+// Twiddle entries: float4 (p, u, s, 0).
+
+__device__ __forceinline__ float2 lift_fwd(float2 a, float4 w) {
+  float x = w.z * a.x, y = w.z * a.y;
+  x = fmaf(w.x, y, x);
+  y = fmaf(w.y, x, y);
+  x = fmaf(w.x, y, x);
+  return float2{x, y};
+}
+__device__ __forceinline__ float2 lift_inv(float2 a, float4 w) {
+  float x = a.x, y = a.y;
+  x = fmaf(-w.x, y, x);
+  y = fmaf(-w.y, x, y);
+  x = fmaf(-w.x, y, x);
+  return float2{w.z * x, w.z * y};
+}
+// Fixed rotations by -pi/4 and +pi/4 (radix 8): p = tan(pi/8) resp. -tan(pi/8), u = -+ sin(pi/4).
+constexpr float LIFT_P8 = 0.41421356237309504880f;
+constexpr float LIFT_U8 = 0.70710678118654752440f;
+template <int SGN> __device__ __forceinline__ float2 rot8_fwd(float2 a) {  // rotation by SGN * pi/4
+  float x = a.x, y = a.y;
+  x = fmaf(-SGN * LIFT_P8, y, x);
+  y = fmaf(SGN * LIFT_U8, x, y);
+  x = fmaf(-SGN * LIFT_P8, y, x);
+  return float2{x, y};
+}
+template <int SGN> __device__ __forceinline__ float2 rot8_inv(float2 a) {  // exact inverse of rot8_fwd<SGN>
+  float x = a.x, y = a.y;
+  x = fmaf(SGN * LIFT_P8, y, x);
+  y = fmaf(-SGN * LIFT_U8, x, y);
+  x = fmaf(SGN * LIFT_P8, y, x);
+  return float2{x, y};
+}
+
+// Forward radix-8 butterfly (exp(-2 pi i / 8) kernel) with lifted rotations:
+// e = DFT4(v0, v2, v4, v6), o = DFT4(v1, v3, v5, v7); o_k *= exp(-i pi k / 4) (k = 1: rotation by
+// -pi/4; k = 2: -i, exact; k = 3: minus a rotation by +pi/4, the sign taken by the combination).
+template <int S> __device__ __forceinline__ void bfly8_lf(float2* v) {
+  float2 e[4] = {v[0], v[2 * S], v[4 * S], v[6 * S]};
+  float2 o[4] = {v[S], v[3 * S], v[5 * S], v[7 * S]};
+  bfly4<-1, 1>(e);
+  bfly4<-1, 1>(o);
+  o[1] = rot8_fwd<-1>(o[1]);
+  o[2] = rot<-1>(o[2]);
+  o[3] = rot8_fwd<+1>(o[3]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    v[k * S] = cadd(e[k], o[k]);
+    v[(k + 4) * S] = csub(e[k], o[k]);
+  }
+  v[3 * S] = csub(e[3], o[3]);
+  v[7 * S] = cadd(e[3], o[3]);
+}
+// Its inverse times 8.
+template <int S> __device__ __forceinline__ void ibfly8_lf(float2* v) {
+  float2 e[4], o[4];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    e[k] = cadd(v[k * S], v[(k + 4) * S]);
+    o[k] = csub(v[k * S], v[(k + 4) * S]);
+  }
+  e[3] = cadd(v[3 * S], v[7 * S]);
+  o[3] = csub(v[7 * S], v[3 * S]);
+  o[1] = rot8_inv<-1>(o[1]);
+  o[2] = rot<+1>(o[2]);
+  o[3] = rot8_inv<+1>(o[3]);
+  bfly4<+1, 1>(e);
+  bfly4<+1, 1>(o);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[2 * k * S] = e[k];
+    v[(2 * k + 1) * S] = o[k];
+  }
+}
+template <int R, int S> __device__ __forceinline__ void bfly_lf(float2* v) {
+  if constexpr (R == 8) bfly8_lf<S>(v);
+  else bfly<R, -1, S>(v);
+}
+// Inverse butterfly times R: radix 2 and 4 are symmetric with exact constants (the conjugate
+// kernel inverts them); radix 3 and 5 too, to the double-single accuracy of their constants.
+template <int R, int S> __device__ __forceinline__ void ibfly_lf(float2* v) {
+  if constexpr (R == 8) ibfly8_lf<S>(v);
+  else bfly<R, +1, S>(v);
+}
+
+// Stage s of the plan: NS = product of the radices of the stages before it.
+__host__ __device__ constexpr int stage_ns(int N, int E, int S) {
+  int ns = 1;
+  for (int i = 0; i < S; ++i) ns *= pick_radix(N / ns, E);
+  return ns;
+}
+
+// Forward transform of NL lines (as lines_fft with DIR = -1), lifted twiddles.
+template <int N, int E, int NBAR, int NL, int NS = 1, int IX = 0, bool PP = false, int CNS = 0>
+__device__ __forceinline__ void lines_fft_lf(float2 (*v)[E], float2* sm, int SS, int LS, int t, const float4* tw,
+                                             float2* sm2 = nullptr, const float4* twr = nullptr) {
+  if constexpr (NS < N) {
+    constexpr int P = N / E;
+    constexpr int R = pick_radix(N / NS, E);
+    static_assert(R > 0, "no factorisation for this (N, E)");
+    constexpr int B = E / R;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + P * b;
+      const int k = j % NS;
+      if constexpr (NS > 1) {
+        constexpr int OFF = tw_stage_off(N, E, NS);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const float4 w = NS == CNS ? twr[b * (R - 1) + r - 1] : tw[OFF + (r - 1) * NS + k];
+#pragma unroll
+          for (int l = 0; l < NL; ++l) v[l][b + r * B] = lift_fwd(v[l][b + r * B], w);
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < NL; ++l) bfly_lf<R, B>(v[l] + b);
+    }
+    if constexpr (NS * R < N) {
+      float2* xb = (PP && (IX & 1)) ? sm2 : sm;
+      constexpr int NX = num_stages(N, E) - 1;
+      if constexpr (!(PP && (IX > 0 || NX % 2 == 0))) fft_bar<NBAR>();
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int j = t + P * b;
+        const int k = j % NS;
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int l = 0; l < NL; ++l)
+#pragma unroll
+          for (int r = 0; r < R; ++r) xb[l * LS + xoff(base + r * NS, SS)] = v[l][b + r * B];
+      }
+      fft_bar<NBAR>();
+#pragma unroll
+      for (int l = 0; l < NL; ++l)
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[l][m] = xb[l * LS + xoff(t + P * m, SS)];
+      lines_fft_lf<N, E, NBAR, NL, NS * R, IX + 1, PP, CNS>(v, sm, SS, LS, t, tw, sm2, twr);
+    }
+  }
+}
+
+// The mirror of lines_fft_lf (times N): stage S = num_stages - 1 down to 0.  Thread t holds the
+// frequencies t + P m on entry and the positions t + P m on exit, like lines_fft.  Exchanges
+// (IX counts them in execution order) alternate between sm and sm2 under PP as in lines_fft.
+template <int N, int E, int NBAR, int NL, int S = num_stages(N, E) - 1, int IX = 0, bool PP = false, int CNS = 0>
+__device__ __forceinline__ void lines_ifft_lf(float2 (*v)[E], float2* sm, int SS, int LS, int t, const float4* tw,
+                                              float2* sm2 = nullptr, const float4* twr = nullptr) {
+  if constexpr (S >= 0) {
+    constexpr int P = N / E;
+    constexpr int NS = stage_ns(N, E, S);
+    constexpr int R = pick_radix(N / NS, E);
+    constexpr int B = E / R;
+    constexpr int NX = num_stages(N, E) - 1;
+    constexpr int IXN = (NS * R < N) ? IX + 1 : IX;
+    if constexpr (NS * R < N) {
+      // undo the exchange that followed this stage: natural positions out, the stage's in
+      float2* xb = (PP && (IX & 1)) ? sm2 : sm;
+      if constexpr (!(PP && (IX > 0 || NX % 2 == 0))) fft_bar<NBAR>();
+#pragma unroll
+      for (int l = 0; l < NL; ++l)
+#pragma unroll
+        for (int m = 0; m < E; ++m) xb[l * LS + xoff(t + P * m, SS)] = v[l][m];
+      fft_bar<NBAR>();
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int j = t + P * b;
+        const int k = j % NS;
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int l = 0; l < NL; ++l)
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[l][b + r * B] = xb[l * LS + xoff(base + r * NS, SS)];
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + P * b;
+      const int k = j % NS;
+#pragma unroll
+      for (int l = 0; l < NL; ++l) ibfly_lf<R, B>(v[l] + b);
+      if constexpr (NS > 1) {
+        constexpr int OFF = tw_stage_off(N, E, NS);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const float4 w = NS == CNS ? twr[b * (R - 1) + r - 1] : tw[OFF + (r - 1) * NS + k];
+#pragma unroll
+          for (int l = 0; l < NL; ++l) v[l][b + r * B] = lift_inv(v[l][b + r * B], w);
+        }
+      }
+    }
+    lines_ifft_lf<N, E, NBAR, NL, S - 1, IXN, PP, CNS>(v, sm, SS, LS, t, tw, sm2, twr);
+  }
+}
+
 }  // namespace mx

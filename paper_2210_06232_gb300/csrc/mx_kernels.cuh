@@ -17,6 +17,8 @@
 //                     any other.  The spectrum therefore holds exactly as
 //                     many reals as the physical fields.
 #pragma once
+#include <type_traits>
+
 #include "mx_fft.cuh"
 #include "mx_tma.cuh"
 
@@ -567,7 +569,10 @@ struct ZTile {
   // unpadded exchange buffer with swizzled rows (swz_rows): XK + 1 rows of TX values per 128-byte line
   static constexpr size_t xbuf_bytes = (size_t)N * TX * sizeof(cx<T>);
   static constexpr int XK = TX * (int)sizeof(cx<T>) >= 128 ? 0 : 128 / (TX * (int)sizeof(cx<T>)) - 1;
-  static constexpr size_t coef_bytes = (size_t)E * NT * 32;  // staged coefficient entries (32 bytes each)
+  // staged coefficient entries (32 bytes each): one per column and |m_z| = 0 .. N/2 - 1 (the entry
+  // depends on m_z^2 only, and the Nyquist plane has m_z = 0), shared by the threads that need it
+  static constexpr int NA = N / 2;
+  static constexpr size_t coef_bytes = (size_t)NA * TX * 32;
   // components in threes: the forward transforms exchange through the last two buffers' worth of
   // the input stage and one more right after it, the inverse ones through six in the output stage
   static constexpr bool TRIP = XK <= 7 && N % (XK + 1) == 0 && coef_bytes + 2 * xbuf_bytes <= stage_bytes &&
@@ -606,6 +611,24 @@ __device__ __forceinline__ void z_tile_copy(const void* tmap, cx<T>* stage, uint
   for (int h = 0; h < ZT::NZC; ++h)
     tma_load_4d(reinterpret_cast<unsigned char*>(stage) + h * (ZT::stage_bytes / ZT::NZC), tmap, 2 * x0, y, h * ZT::ZC, 0,
                 full);
+}
+
+// Forward and inverse z transforms of NL components in the fused pass: in FP32 the exactly
+// invertible pair (lifted rotations, mirrored inverse; mx_fft.cuh), whose twiddle table holds
+// lifting constants; in FP64 the plain pair (constants rounded to FP64 bias a step by ~1e-16).
+template <typename T, int N, int E, int NL, bool PP = false, int CNS = 0>
+__device__ __forceinline__ void zf_fwd(cx<T> (*v)[E], cx<T>* sm, int SS, int LS, int t, const twv<T>* tw,
+                                       cx<T>* sm2 = nullptr, const twv<T>* twr = nullptr) {
+  if constexpr (std::is_same<T, float>::value) lines_fft_lf<N, E, 0, NL, 1, 0, PP, CNS>(v, sm, SS, LS, t, tw, sm2, twr);
+  else lines_fft<T, N, E, -1, 0, NL, 1, 0, PP, CNS>(v, sm, SS, LS, t, tw, sm2, twr);
+}
+template <typename T, int N, int E, int NL, bool PP = false, int CNS = 0>
+__device__ __forceinline__ void zf_inv(cx<T> (*v)[E], cx<T>* sm, int SS, int LS, int t, const twv<T>* tw,
+                                       cx<T>* sm2 = nullptr, const twv<T>* twr = nullptr) {
+  if constexpr (std::is_same<T, float>::value)
+    lines_ifft_lf<N, E, 0, NL, num_stages(N, E) - 1, 0, PP, CNS>(v, sm, SS, LS, t, tw, sm2, twr);
+  else
+    lines_fft<T, N, E, +1, 0, NL, 1, 0, PP, CNS>(v, sm, SS, LS, t, tw, sm2, twr);
 }
 
 // SRC: where the coefficients come from: 0 = the table (tab set), 1 = computed per point in FP64
@@ -684,22 +707,26 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       __syncthreads();  // twiddles
     }
     const int my = signed_index(y, g.ny);
-    // TMAP: the input stage is free until the next tile's copy; this thread's coefficient-table
-    // entries are copied into it (cp.async) while the forward transforms run, as planes of 16-byte
-    // pieces (piece h of entry m of thread i at cpl[(h E + m) NT + i]), so that a warp's copies and
-    // reads of one piece are 512 contiguous bytes
+    // TMAP: the input stage is free until the next tile's copy; the tile's coefficient-table
+    // entries, one per column and |m_z| (ZTile::NA of them per column), are copied into it
+    // (cp.async, spread over all threads) while the forward transforms run, as planes of 16-byte
+    // pieces (piece h of the entry of column x and |m_z| = a at cpl[(h NA + a) TX + x]): a warp's
+    // copies are contiguous, and its reads of one piece (consecutive or mirrored |m_z|) too
     constexpr int NPC = (int)(sizeof(CoefT) / 16);
+    constexpr int NA = ZT::NA;
     static_assert(sizeof(CoefT) % 16 == 0, "coefficient entries are whole 16-byte pieces");
     float4* cpl = reinterpret_cast<float4*>(stage);
-    static_assert((size_t)E * ZT::NT * sizeof(CoefT) <= ZT::stage_bytes, "coefficients fit in the stage");
-    const bool staged = TMAP && tab != nullptr && ok;
+    static_assert((size_t)NA * TX * sizeof(CoefT) <= ZT::stage_bytes, "coefficients fit in the stage");
+    const bool staged = TMAP && tab != nullptr;  // block-uniform
     if (staged) {
+      const int col0 = col - x;
+      const int qyy = g.qa[1] * my * my;
 #pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const int mz = signed_index(t + P * m, N);
-        const float4* src = reinterpret_cast<const float4*>(tab + (g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz));
-#pragma unroll
-        for (int h = 0; h < NPC; ++h) cp_async_16n<16>(cpl + (h * E + m) * ZT::NT + threadIdx.x, src + h);
+      for (int L = threadIdx.x; L < NPC * NA * TX; L += ZT::NT) {
+        const int xx = L % TX, a = (L / TX) % NA, h = L / (TX * NA);
+        const int cx = col0 + xx;
+        if (cx < g.mx)
+          cp_async_16n<16>(cpl + L, reinterpret_cast<const float4*>(tab + (g.qa[0] * cx * cx + qyy + g.qa[2] * a * a)) + h);
       }
       cp_async_commit();
     }
@@ -712,18 +739,21 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       C* fb = reinterpret_cast<C*>(zsmraw + ZT::stage_bytes - 2 * ZT::xbuf_bytes);
 #pragma unroll
       for (int c = 0; c < 6; c += 3)
-        lines_fft<T, N, E, -1, 0, 3, 1, 0, false, TWC>(v + c, fb + x, SWZ, LX, t, tw, nullptr, twr);
-    } else if constexpr (TMAP && (size_t)E * ZT::NT * sizeof(CoefT) + ZT::exch_bytes <= ZT::stage_bytes) {
+        zf_fwd<T, N, E, 3, false, TWC>(v + c, fb + x, SWZ, LX, t, tw, nullptr, twr);
+    } else if constexpr (TMAP && ZT::coef_bytes + ZT::exch_bytes <= ZT::stage_bytes) {
       // two components at a time: the second exchange buffer is the input stage past the coefficients
-      C* xb2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(stage) + (size_t)E * ZT::NT * sizeof(CoefT));
+      C* xb2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(stage) + ZT::coef_bytes);
       const int ls2 = (int)(xb2 - sm);
 #pragma unroll
-      for (int c = 0; c < 6; c += 2) lines_fft<T, N, E, -1, 0, 2>(v + c, sm + x, TX, ls2, t, tw);
+      for (int c = 0; c < 6; c += 2) zf_fwd<T, N, E, 2>(v + c, sm + x, TX, ls2, t, tw);
     } else {
 #pragma unroll
-      for (int c = 0; c < 6; c += ZT::NL) lines_fft<T, N, E, -1, 0, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
+      for (int c = 0; c < 6; c += ZT::NL) zf_fwd<T, N, E, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
     }
-    if (staged) cp_async_wait_all();
+    if (staged) {
+      cp_async_wait_all();
+      __syncthreads();  // every thread's copies have landed (a thread reads entries others copied)
+    }
     T part[INV ? 16 : 1];  // NSUM sums and a zero (warp_transpose_sum16)
 #pragma unroll
     for (int k = 0; k < (INV ? 16 : 1); ++k) part[k] = (T)0;
@@ -739,8 +769,9 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
             CoefT c;
             float4 f[NPC];
           } u;
+          const int a = mz < 0 ? -mz : mz;
 #pragma unroll
-          for (int h = 0; h < NPC; ++h) u.f[h] = cpl[(h * E + m) * ZT::NT + threadIdx.x];
+          for (int h = 0; h < NPC; ++h) u.f[h] = cpl[(h * NA + a) * TX + x];
           return u.c;
         };
         auto direct = [&]() {
@@ -751,7 +782,7 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
         if constexpr (SRC == 1) {
           q = direct();
         } else if constexpr (SRC == 0 && TMAP) {
-          q = from_stage();  // staged: the table is set and this column is inside the grid
+          q = from_stage();  // staged: the table is set (and this column is inside the grid)
         } else if constexpr (SRC == 0) {
           q = tab[g.qa[0] * col * col + g.qa[1] * my * my + g.qa[2] * mz * mz];
         } else {
@@ -793,7 +824,7 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       // triplets of buffers there, so that none waits for the readers of the one before it
 #pragma unroll
       for (int c = 0; c < 6; c += 3)
-        lines_fft<T, N, E, +1, 0, 3, 1, 0, true, TWC>(v + c, ostage + x, SWZ, LX, t, tw, ostage + 3 * LX + x, twr);
+        zf_inv<T, N, E, 3, true, TWC>(v + c, ostage + x, SWZ, LX, t, tw, ostage + 3 * LX + x, twr);
     } else if constexpr (TMAP) {
       // two components at a time through the output stage: exchanges alternate between two pairs
       // of buffers there, so that none waits for the readers of the one before it
@@ -801,15 +832,15 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
       if constexpr (4 * ZT::exch_bytes <= ZT::stage_bytes) {
 #pragma unroll
         for (int c = 0; c < 6; c += 2)
-          lines_fft<T, N, E, +1, 0, 2, 1, 0, true>(v + c, ostage + x, TX, LS, t, tw, ostage + 2 * LS + x);
+          zf_inv<T, N, E, 2, true>(v + c, ostage + x, TX, LS, t, tw, ostage + 2 * LS + x);
       } else {
         const int ls2 = (int)(ostage - sm);
 #pragma unroll
-        for (int c = 0; c < 6; c += 2) lines_fft<T, N, E, +1, 0, 2>(v + c, sm + x, TX, ls2, t, tw);
+        for (int c = 0; c < 6; c += 2) zf_inv<T, N, E, 2>(v + c, sm + x, TX, ls2, t, tw);
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < 6; c += ZT::NL) lines_fft<T, N, E, +1, 0, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
+      for (int c = 0; c < 6; c += ZT::NL) zf_inv<T, N, E, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
     }
     if constexpr (TMAP) {
       // through the output stage and the tensor-copy engine (it drops the columns past Mx)

@@ -103,6 +103,7 @@ def _load():
         "mx_debug_fail_alloc": (I, [LL]),
         "mx_debug_wait_limit": (I, [P, LL]),
         "mx_fma_peak": (I, [I, C.POINTER(D)]),
+        "mx_dft8_stage_eval": (I, [I, V, V, LL, I, C.POINTER(D)]),
         "mx_sync": (I, [P]),
         "mx_strerror": (C.c_char_p, [I]),
         "mx_destroy": (None, [P]),
@@ -151,6 +152,7 @@ mx_profile_read = _lib.mx_profile_read
 mx_debug_fail_alloc = _lib.mx_debug_fail_alloc
 mx_debug_wait_limit = _lib.mx_debug_wait_limit
 mx_fma_peak = _lib.mx_fma_peak
+mx_dft8_stage_eval = _lib.mx_dft8_stage_eval
 
 
 def fma_peak(precision):
