@@ -46,10 +46,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--grid", type=int, default=512, help="cubic grid size (default 512)")
+    ap.add_argument("--shape", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
+                    help="a non-cubic grid for the headline form only (small profiling cases; implies "
+                         "--no-secondary)")
     ap.add_argument("--no-secondary", action="store_true", help="skip the FP64 and literal-form lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
-    ap.add_argument("--only", choices=["dft8"], default=None,
-                    help="dft8: only the tensor-core DFT-as-GEMM evaluation (one JSON line; for profiling)")
+    ap.add_argument("--only", choices=["dft8", "batch"], default=None,
+                    help="dft8: only the tensor-core DFT-as-GEMM evaluation; batch: only the batched form "
+                         "(config 4, spectral; --steps steps); one JSON line, for profiling")
     return ap.parse_args()
 
 
@@ -143,6 +147,9 @@ def timed_steps(torch, solver, stream, h, steps, warmup, dist=None, clocks=None)
     torch.cuda.synchronize()
     if clocks:
         clocks.start()
+    ncu_range = bool(os.environ.get("MX_NCU_RANGE"))  # profiler range around the timed steps (ncu --profile-from-start off)
+    if ncu_range:
+        torch.cuda.profiler.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -150,6 +157,8 @@ def timed_steps(torch, solver, stream, h, steps, warmup, dist=None, clocks=None)
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize()
+    if ncu_range:
+        torch.cuda.profiler.stop()
     ck = clocks.stop() if clocks else None
     if dist is not None:
         dist.barrier()
@@ -197,10 +206,15 @@ KERNEL_SOURCES = {
 }
 
 
+def npoints(grid):
+    """Grid points of a cubic size or an (nx, ny, nz) shape."""
+    return int(np.prod(grid)) if isinstance(grid, (tuple, list)) else grid ** 3
+
+
 def pass_bytes(kind, grid, es):
     """Algorithmic bytes of one launch of a pass over all six components: read and write six components'
-    worth of the packed half spectrum (grid^3 / 2 complex values each), equal to six real fields."""
-    return 12 * (grid ** 3 // 2) * 2 * es
+    worth of the packed half spectrum (N_S / 2 complex values each), equal to six real fields."""
+    return 12 * (npoints(grid) // 2) * 2 * es
 
 
 def traffic_for(key):
@@ -230,7 +244,7 @@ def source_sha(kind):
 
 # ------------------------------------------------------------------ forms
 def run_form(torch, mx, grid, precision, form, steps, warmup, stream, dist=None, clocks=None, keep=False):
-    n = (grid, grid, grid)
+    n = tuple(grid) if isinstance(grid, (tuple, list)) else (grid, grid, grid)
     lo, hi = (0.0, 0.0, 0.0), (2 * np.pi,) * 3
     s = mx.Solver(n, lo, hi, 1.0, 1.0, precision, form, stream=stream)
     s.autotune()  # kernel variant and grid per pass of this shape (cached per process)
@@ -258,13 +272,13 @@ def step_flops(grid, form):
     """Algorithmic flops of one step: 2.5 N log2 N per real 3D transform of N = grid^3 points (half the
     classic 5 N log2 N of a complex one), six fields forward and inverse in the literal form (none in the
     spectral-resident form), plus the update and the invariant sums at every k-point."""
-    ns = grid ** 3
+    ns = npoints(grid)
     fft = 0.0 if form == 1 else 6 * 2 * 2.5 * ns * np.log2(ns)
     return fft + (ns / 2) * (UPDATE_FLOPS_PER_K + INVARIANT_FLOPS_PER_K)
 
 
 def form_entry(name, grid, precision, form, ms, steps, prof, peak, inv, world, alu_peak=None):
-    ns = grid ** 3
+    ns = npoints(grid)
     es = 8 if precision == 0 else 4
     step_ms = ms / steps
     value = world * ns * steps / (ms / 1e3)
@@ -294,15 +308,18 @@ def form_entry(name, grid, precision, form, ms, steps, prof, peak, inv, world, a
 BATCH_SHAPES = [(32, 32, 32), (48, 64, 80), (64, 64, 64), (96, 96, 64), (128, 128, 128)]
 
 
-def batch_run(torch, mx, peak, steps, warmup, stream, ninst=64, seed=4):
-    """Batched form: 64 FP32 instances of uneven grids, eps, mu in [1, 4], h in [0.01, 0.1], sigma = 8;
-    every step of every instance in one persistent cooperative launch per mx_batch_step call."""
+def batch_run(torch, mx, peak, steps, warmup, stream, ninst=64, seed=4, form=None):
+    """Batched form: 64 FP32 instances of uneven grids, eps, mu in [1, 4], h in [0.01, 0.1], sigma = 8.
+    Spectral form: every step of every instance in one persistent cooperative launch per mx_batch_step
+    call.  Literal form: each instance's autotuned x, y, fused z, y, x passes per step, all instances as
+    parallel branches of one CUDA graph per call."""
+    form = mx.MX_FORM_SPECTRAL if form is None else form
     rng = np.random.default_rng(seed)
     specs = []
     for _ in range(ninst):
         n = BATCH_SHAPES[rng.integers(len(BATCH_SHAPES))]
         specs.append(dict(n=n, eps=float(rng.uniform(1, 4)), mu=float(rng.uniform(1, 4)), h=float(rng.uniform(0.01, 0.1))))
-    b = mx.Batch(specs, mx.MX_FP32, stream=stream)
+    b = mx.Batch(specs, mx.MX_FP32, stream=stream, form=form)
     b.load_random(seed, 8.0)
     b.step(steps, 1)  # warm-up call: captures the graph for this step count
     b.sync()
@@ -325,6 +342,8 @@ def batch_run(torch, mx, peak, steps, warmup, stream, ninst=64, seed=4):
     b.close()
     min_bytes = 12 * pts * 4
     return {
+        "form": "literal (graph of per-instance pass chains)" if form == mx.MX_FORM_LITERAL
+                else "spectral-resident (one persistent launch)",
         "value": pts * steps / (ms / 1e3),
         "unit": UNIT,
         "ms_per_step": ms / steps,
@@ -340,12 +359,15 @@ def batch_run(torch, mx, peak, steps, warmup, stream, ninst=64, seed=4):
 
 
 SERVE_SHAPES = [(32, 32, 32), (64, 64, 64), (96, 96, 96), (128, 128, 128), (192, 192, 192)]
+# offered rate of the multi-step scenario (mean ~650 steps per request): about what one GB300 sustains
+SERVE_MULTISTEP_RATE = 8.0
 
 
-def serve_run(torch, mx, duration=5.0, rate=200.0, seed=5, budget=32 << 30):
-    """Serving form: Poisson arrivals (mean `rate`/s) of one-step solves (the paper's single step of size
-    t_end) with grids from SERVE_SHAPES, t_end ~ U[1, 50], eps, mu ~ U[1, 4], FP32 or FP64 (50/50), random
-    divergence-free initial fields; p50/p99 latency (submission to completion) and solves/s."""
+def serve_run(torch, mx, duration=5.0, rate=200.0, seed=5, budget=32 << 30, multistep=False):
+    """Serving form: Poisson arrivals (mean `rate`/s) of solves with grids from SERVE_SHAPES, t_end ~ U[1, 50],
+    eps, mu ~ U[1, 4], FP32 or FP64 (50/50), random divergence-free initial fields; p50/p99 latency (submission
+    to completion), solves/s and the device concurrency the server recorded.  multistep=False: each request is
+    the paper's single step of size t_end; True: ceil(t_end / h) steps with h ~ U[0.01, 0.1]."""
     import threading
 
     rng = np.random.default_rng(seed)
@@ -365,12 +387,12 @@ def serve_run(torch, mx, duration=5.0, rate=200.0, seed=5, budget=32 << 30):
     free = {k: list(v) for k, v in outs.items()}
     lock = threading.Lock()
 
-    def submit(sh, prec, t_end, eps, mu):
+    def submit(sh, prec, t_end, eps, mu, nsteps=1):
         E0, H0 = inputs[(sh, prec)]
         with lock:
             pool = free[(sh, prec)]
             Eo, Ho = pool.pop() if pool else (torch.empty_like(E0).pin_memory(), torch.empty_like(H0).pin_memory())
-        rid = srv.submit(sh, E0, H0, Eo, Ho, t_end, eps, mu, prec, 1, 0)
+        rid = srv.submit(sh, E0, H0, Eo, Ho, t_end, eps, mu, prec, nsteps, 0)
         return rid, (sh, prec, Eo, Ho)
 
     def release(tag):
@@ -388,8 +410,13 @@ def serve_run(torch, mx, duration=5.0, rate=200.0, seed=5, budget=32 << 30):
     # arrivals
     n = int(duration * rate)
     gaps = rng.exponential(1.0 / rate, size=n)
-    plan = [(SERVE_SHAPES[rng.integers(len(SERVE_SHAPES))], mx.MX_FP32 if rng.random() < 0.5 else mx.MX_FP64,
-             float(rng.uniform(1, 50)), float(rng.uniform(1, 4)), float(rng.uniform(1, 4))) for _ in range(n)]
+    plan = []
+    for _ in range(n):
+        sh = SERVE_SHAPES[rng.integers(len(SERVE_SHAPES))]
+        prec = mx.MX_FP32 if rng.random() < 0.5 else mx.MX_FP64
+        t_end, eps, mu = float(rng.uniform(1, 50)), float(rng.uniform(1, 4)), float(rng.uniform(1, 4))
+        nsteps = int(np.ceil(t_end / rng.uniform(0.01, 0.1))) if multistep else 1
+        plan.append((sh, prec, t_end, eps, mu, nsteps))
     import queue as _q
 
     pending = _q.Queue()
@@ -411,12 +438,12 @@ def serve_run(torch, mx, duration=5.0, rate=200.0, seed=5, budget=32 << 30):
     th.start()
     t0 = time.perf_counter()
     due = t0
-    for gap, (sh, prec, t_end, eps, mu) in zip(gaps, plan):
+    for gap, (sh, prec, t_end, eps, mu, nsteps) in zip(gaps, plan):
         due += gap
         now = time.perf_counter()
         if due > now:
             time.sleep(due - now)
-        pending.put(submit(sh, prec, t_end, eps, mu))
+        pending.put(submit(sh, prec, t_end, eps, mu, nsteps))
     t_sub = time.perf_counter()
     pending.put(None)
     th.join()
@@ -425,7 +452,15 @@ def serve_run(torch, mx, duration=5.0, rate=200.0, seed=5, budget=32 << 30):
     st = srv.stats()
     srv.close()
     lat = np.array(lat)
+    steps_total = sum(p[5] for p in plan)
     return {
+        "device_concurrency": {"max_requests": st["max_concurrent"], "mean_requests_while_busy": st["mean_concurrent"],
+                               "busy_s": st["busy_s"], "sum_request_s": st["request_s_sum"],
+                               "overlap": st["request_s_sum"] / st["busy_s"] if st["busy_s"] > 0 else None,
+                               "what": "requests admitted and not finished at once (time-weighted over the time "
+                                       "at least one was); overlap = summed admission-to-completion time / busy "
+                                       "time (1: one at a time)"},
+        "steps_per_request_mean": steps_total / max(n, 1),
         "requests": n,
         "completed": ok,
         "offered_rate_per_s": rate,
@@ -437,8 +472,9 @@ def serve_run(torch, mx, duration=5.0, rate=200.0, seed=5, budget=32 << 30):
         "hbm_budget_gb": budget / 1e9,
         "hbm_high_water_gb": st["hbm_high_water"] / 1e9,
         "rejected": st["rejected"],
-        "work": "one exponential step of size t_end per request (Sec. 2.5), load + solve + read through "
-                "pinned host buffers; grids 32^3..192^3, FP32/FP64 50/50, t_end ~ U[1,50]",
+        "work": ("ceil(t_end / h) steps, h ~ U[0.01, 0.1], per request" if multistep else
+                 "one exponential step of size t_end per request (Sec. 2.5)") +
+                ", load + solve + read through pinned host buffers; grids 32^3..192^3, FP32/FP64 50/50, t_end ~ U[1,50]",
     }
 
 
@@ -703,6 +739,10 @@ def main():
     if args.only == "dft8":
         print(json.dumps({"dft_as_gemm_stage": dft_gemm_eval(torch, mx, tiles=2 * 152, reps=64)}), flush=True)
         return
+    if args.only == "batch":
+        st = torch.cuda.Stream()
+        print(json.dumps({"batched": batch_run(torch, mx, peaks()[0], args.steps, args.warmup, st)}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as td
@@ -711,7 +751,9 @@ def main():
         dist = td
     stream = torch.cuda.Stream()
     peak, peak_src = peaks()
-    grid = args.grid
+    grid = tuple(args.shape) if args.shape else args.grid
+    if args.shape:
+        args.no_secondary = True
     clocks = ClockSampler(gpu_smi_id(torch, local))
 
     # headline: FP32 precision form, the whole step (R2C -> update + invariants -> C2R) every step
@@ -720,7 +762,7 @@ def main():
     schedule = sched_s.schedule()
     sched_s.close()
     ms = max_over_ranks(torch, dist, ms)
-    ns = grid ** 3
+    ns = npoints(grid)
     value = whole_job_value(world, ns * args.steps, ms)
     # dominant kernel of the step: every pass reads and writes six components' worth of the
     # packed half spectrum (x passes: six real fields on the other side, the same bytes)
@@ -737,7 +779,7 @@ def main():
         a_gbs = pass_bytes(k, grid, 4) / (k_ms / k_n / 1e3) / 1e9
         per_pass[k] = {"kernel": KERNEL_NAMES.get(k, k), "ms_per_launch": k_ms / k_n,
                        "launches_per_step": k_n / args.steps, "achieved_gbs": a_gbs, "frac": a_gbs / peak,
-                       "traffic": traffic_for(f"{k}_fp32_{grid}")}
+                       "traffic": traffic_for(f"{k}_fp32_{grid}") if not args.shape else None}
     forms = {}
     name, e = form_entry("precision_fp32_literal", grid, mx.MX_FP32, mx.MX_FORM_LITERAL, ms, args.steps, prof, peak,
                          inv, world)
@@ -755,11 +797,18 @@ def main():
             forms[nm] = form_entry(nm, grid, p, f, ms2, k, prof2, peak, inv2, world,
                                    alu_peak=alu["fp64_fma_flops"] if p == mx.MX_FP64 else None)[1]
 
-    e2e = e2e_run(torch, mx, grid, args.steps, stream)
-    batched = None if args.no_secondary else batch_run(torch, mx, peak, min(args.steps, 100), args.warmup, stream)
+    e2e = e2e_run(torch, mx, grid, args.steps, stream) if not args.shape else None
+    batched = None
+    if not args.no_secondary:
+        batched = batch_run(torch, mx, peak, min(args.steps, 100), args.warmup, stream)
+        batched["literal_form"] = batch_run(torch, mx, peak, min(args.steps, 20), args.warmup, stream,
+                                            form=mx.MX_FORM_LITERAL)
     comparison = None if args.no_secondary else {"cufft_transforms": cufft_comparison(torch, grid),
                                                  "dft_as_gemm_stage": dft_gemm_eval(torch, mx)}
-    serve = None if (args.no_secondary or rank != 0) else serve_run(torch, mx)
+    serve = None
+    if not args.no_secondary and rank == 0:
+        serve = serve_run(torch, mx)
+        serve["multistep"] = serve_run(torch, mx, duration=5.0, rate=SERVE_MULTISTEP_RATE, multistep=True)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline_sample()
@@ -782,9 +831,10 @@ def main():
         "dtype": "f32",
         "data": "synthetic: seeded random divergence-free fields, Gaussian spectrum sigma=16 (device generator)",
         "config": {
-            "workload": f"{grid}^3 precision form: FFTs and update in FP32, phase c|k|h and invariant sums in "
+            "workload": f"{'x'.join(map(str, grid)) if args.shape else str(grid) + '^3'} precision form: FFTs and update "
+                        "in FP32, phase c|k|h and invariant sums in "
                         "FP64, eps=mu=1, h=0.02, invariants every step",
-            "grid": [grid] * 3,
+            "grid": list(grid) if args.shape else [grid] * 3,
             "form": "literal: forward 3D R2C, exponential update + invariants, inverse 3D C2R every step",
             "l2": "state 3.2 GB per pass > 129 MB L2: inputs larger than L2, no flush",
             "parallelism": f"replicas x{world}",
@@ -797,7 +847,7 @@ def main():
             "peak_source": peak_src,
             "unit": "GB/s",
             "frac": achieved / peak,
-            "traffic": traffic_for(f"{dom}_fp32_{grid}"),
+            "traffic": traffic_for(f"{dom}_fp32_{grid}") if not args.shape else None,
             "algorithmic_bytes_per_launch": bytes_per_launch,
         },
         "step_hbm_roofline_frac": forms["precision_fp32_literal"]["step_hbm_roofline_frac"],

@@ -213,6 +213,19 @@ typedef struct {
 } mx_instance_desc;
 
 mx_status mx_batch_create(mx_batch** out, const mx_instance_desc* inst, int n, int precision, void* stream);
+/*
+ * The same in either form.  form = MX_FORM_LITERAL: every instance is a
+ * literal-form context (state = the physical fields; each step the 3D R2C,
+ * the fused z pass with the update and invariants, the 3D C2R), autotuned
+ * at creation for its shape (mx_autotune); mx_batch_step(b, K, every) runs
+ * the K steps of all instances as parallel branches of one CUDA graph (one
+ * stream per instance), captured once per (K, every, step phases) and
+ * replayed; the records the graph writes are appended to each instance's
+ * list after the launch.  Instances are bit-identical alone or in any batch.
+ * mx_batch_create is mx_batch_create_form with MX_FORM_SPECTRAL.
+ */
+mx_status mx_batch_create_form(mx_batch** out, const mx_instance_desc* inst, int n, int precision, int form,
+                               void* stream);
 mx_status mx_batch_size(mx_batch* b, int* n);
 /* Context of instance i (owned by the batch: do not destroy it). */
 mx_status mx_batch_instance(mx_batch* b, int i, mx_ctx** ctx);
@@ -264,6 +277,12 @@ typedef struct {
 typedef struct {
   long long submitted, admitted, completed, rejected, queued, active, pooled_contexts;
   size_t hbm_in_use, hbm_high_water, hbm_budget;
+  /* device concurrency since creation: the most requests admitted and not yet
+   * finished at once; busy_s = seconds with at least one; mean_concurrent = their
+   * time-weighted mean count over busy_s; request_s_sum = the sum over finished
+   * requests of admission-to-completion seconds (> busy_s when requests overlap) */
+  long long max_concurrent;
+  double mean_concurrent, busy_s, request_s_sum;
 } mx_server_info;
 
 mx_status mx_server_create(mx_server** out, size_t hbm_budget_bytes, int max_active);

@@ -1,13 +1,23 @@
-// Batched spectral form (C ABI): independent instances of different grids,
-// eps, mu and step sizes, each a spectral-form context, advanced together by
-// one persistent cooperative launch per mx_batch_step call.  The launch
-// (with the upload of the per-instance descriptors) is captured once per
-// step count into a CUDA graph and replayed.
+// Batched forms (C ABI): independent instances of different grids, eps, mu
+// and step sizes, advanced together.
+//  * spectral form: each instance a spectral-form context, all advanced by one
+//    persistent cooperative launch per mx_batch_step call; the launch (with
+//    the upload of the per-instance descriptors) is captured once per step
+//    count into a CUDA graph and replayed.
+//  * literal form: each instance a literal-form context whose transform
+//    passes run the schedules the autotuner picked for its shape; the K steps
+//    of every instance (x, y, fused z, y, x passes per step) are captured as
+//    parallel branches of one CUDA graph (one stream per instance, forked from
+//    and joined to the batch stream) and replayed, so the small instances'
+//    passes overlap on the device.  The graph writes each instance's
+//    invariant records into a region of its own, copied after every replay to
+//    the instance's record list.
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
 #include <map>
+#include <string>
 #include <vector>
 
 #include "mx_batch.cuh"
@@ -31,6 +41,14 @@ struct mx_batch {
   bool own_stream = false;
   std::map<int, cudaGraphExec_t> graphs;  // nsteps -> executable graph
   mx_status err = MX_OK;
+  // literal form
+  int form = MX_FORM_SPECTRAL;
+  std::vector<cudaStream_t> lstreams;      // one per instance
+  std::vector<cudaEvent_t> ldone;          // one per instance (join)
+  cudaEvent_t fork = nullptr;
+  std::vector<double*> grec;               // record region of the graph, per instance
+  std::vector<long long> grec_cap;         // its capacity (records)
+  std::map<std::string, cudaGraphExec_t> lgraphs;  // (K, every, step phases) -> graph
 };
 
 namespace {
@@ -75,18 +93,159 @@ mx_status fail(mx_batch* b, cudaError_t e) {
   return MX_E_CUDA;
 }
 
+// Literal form: the K steps of every instance, each on its own stream forked from and joined to
+// the batch stream (inside a capture: parallel graph branches).  Records go to each instance's
+// graph region (c->rec pointed there for the duration; the caller restores the context state).
+mx_status enqueue_literal(mx_batch* b, long long k, int every) {
+  if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return MX_E_CUDA;
+  for (int i = 0; i < b->n; ++i) {
+    mx_ctx* c = b->ctx[i];
+    if (cudaStreamWaitEvent(b->lstreams[i], b->fork, 0) != cudaSuccess) return MX_E_CUDA;
+    c->stream = b->lstreams[i];
+    const mx_status st = mx_step(c, b->h[i], k, every);
+    c->stream = b->stream;
+    if (st != MX_OK) return st;
+    if (cudaEventRecord(b->ldone[i], b->lstreams[i]) != cudaSuccess) return MX_E_CUDA;
+    if (cudaStreamWaitEvent(b->stream, b->ldone[i], 0) != cudaSuccess) return MX_E_CUDA;
+  }
+  return MX_OK;
+}
+
+struct CtxState {
+  double* rec;
+  long long rec_n, rec_cap;
+  std::vector<double> rec_t;
+  std::vector<long long> rec_step;
+  double t;
+  long long step;
+  bool prof_on;
+};
+
+mx_status step_literal(mx_batch* b, long long k, int every) {
+  std::vector<long long> nrec(b->n, 0);
+  std::string key = std::to_string(k) + ":" + std::to_string(every);
+  for (int i = 0; i < b->n; ++i) {
+    mx_ctx* c = b->ctx[i];
+    if (c->err != MX_OK) return c->err;
+    if (every > 0) {
+      nrec[i] = (c->step + k) / every - c->step / every;
+      key += ":" + std::to_string(c->step % every);
+    }
+    if (nrec[i] > b->grec_cap[i]) {  // the graph region of this instance (graphs captured before refer to the old one)
+      for (auto& kv : b->lgraphs) cudaGraphExecDestroy(kv.second);
+      b->lgraphs.clear();
+      if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MX_E_CUDA;
+      if (b->grec[i]) cudaFree(b->grec[i]);
+      b->grec[i] = nullptr;
+      b->grec_cap[i] = 0;
+      if (mx::dev_alloc((void**)&b->grec[i], (size_t)nrec[i] * 16 * sizeof(double)) != cudaSuccess) return MX_E_NOMEM;
+      b->grec_cap[i] = nrec[i];
+    }
+  }
+  // the contexts as the graph sees them: records into the graph regions, the table recomputed
+  // inside the graph, no profiling events
+  std::vector<CtxState> saved(b->n);
+  auto redirect = [&]() {
+    for (int i = 0; i < b->n; ++i) {
+      mx_ctx* c = b->ctx[i];
+      saved[i] = CtxState{c->rec, c->rec_n, c->rec_cap, c->rec_t, c->rec_step, c->t, c->step, c->prof_on};
+      c->rec = b->grec[i];
+      c->rec_n = 0;
+      c->rec_cap = b->grec_cap[i];
+      c->rec_t.clear();
+      c->rec_step.clear();
+      c->prof_on = false;
+      c->tab_t = NAN;
+    }
+  };
+  auto restore = [&]() {
+    for (int i = 0; i < b->n; ++i) {
+      mx_ctx* c = b->ctx[i];
+      c->rec = saved[i].rec;
+      c->rec_n = saved[i].rec_n;
+      c->rec_cap = saved[i].rec_cap;
+      c->rec_t.swap(saved[i].rec_t);
+      c->rec_step.swap(saved[i].rec_step);
+      c->t = saved[i].t;
+      c->step = saved[i].step;
+      c->prof_on = saved[i].prof_on;
+    }
+  };
+  mx_status st = MX_OK;
+  if (b->use_graph) {
+    auto it = b->lgraphs.find(key);
+    if (it == b->lgraphs.end()) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      redirect();
+      cudaError_t ce = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      if (ce == cudaSuccess) {
+        st = enqueue_literal(b, k, every);
+        ce = cudaStreamEndCapture(b->stream, &graph);
+      }
+      restore();
+      if (st == MX_OK && ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (st != MX_OK || ce != cudaSuccess) {
+        cudaGetLastError();  // capture refused: launch directly from now on
+        b->graph_err = ce != cudaSuccess ? (int)ce : (int)cudaErrorUnknown;
+        b->use_graph = false;
+        st = MX_OK;
+      } else {
+        it = b->lgraphs.emplace(key, exec).first;
+      }
+    }
+    if (b->use_graph && cudaGraphLaunch(it->second, b->stream) != cudaSuccess) return MX_E_CUDA;
+  }
+  if (!b->use_graph) {
+    redirect();
+    st = enqueue_literal(b, k, every);
+    restore();
+    if (st != MX_OK) return st;
+  }
+  // records of this call: from the graph regions to the instances' record lists
+  for (int i = 0; i < b->n; ++i) {
+    mx_ctx* c = b->ctx[i];
+    const long long n0 = c->step;
+    if (nrec[i] > 0) {
+      st = mx_ensure_records(c, nrec[i]);
+      if (st != MX_OK) return st;
+      if (cudaMemcpyAsync(c->rec + (size_t)c->rec_n * 16, b->grec[i], (size_t)nrec[i] * 16 * sizeof(double),
+                          cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+        return MX_E_CUDA;
+      for (long long N = (n0 / every + 1) * every; N <= n0 + k; N += every) {
+        c->rec_t.push_back(c->t + (double)(N - n0) * b->h[i]);
+        c->rec_step.push_back(N);
+        ++c->rec_n;
+      }
+    }
+    c->t += (double)k * b->h[i];
+    c->step += k;
+    c->tab_t = b->h[i];  // the graph left the table of h in place
+    c->tab_kind = -1;    // (recomputed by the next direct step of the instance)
+  }
+  return MX_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 mx_status mx_batch_create(mx_batch** out, const mx_instance_desc* inst, int n, int precision, void* stream) {
+  return mx_batch_create_form(out, inst, n, precision, MX_FORM_SPECTRAL, stream);
+}
+
+mx_status mx_batch_create_form(mx_batch** out, const mx_instance_desc* inst, int n, int precision, int form,
+                               void* stream) {
   if (!out) return MX_E_INVAL;
   *out = nullptr;
   if (!inst || n < 1 || n > 4096) return MX_E_INVAL;
   if (precision != MX_FP64 && precision != MX_FP32) return MX_E_INVAL;
+  if (form != MX_FORM_SPECTRAL && form != MX_FORM_LITERAL) return MX_E_INVAL;
   mx_batch* b = new mx_batch();
   b->n = n;
   b->prec = precision;
+  b->form = form;
   b->stream = (cudaStream_t)stream;
   if (!b->stream) {  // the legacy default stream cannot be captured into a graph: use an own stream
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -100,6 +259,30 @@ mx_status mx_batch_create(mx_batch** out, const mx_instance_desc* inst, int n, i
     mx_batch_destroy(b);
     return s;
   };
+  if (form == MX_FORM_LITERAL) {
+    for (int i = 0; i < n; ++i) {
+      if (!isfinite(inst[i].h)) return bail(MX_E_INVAL);
+      mx_ctx* c = nullptr;
+      mx_status st = mx_create(&c, inst[i].nx, inst[i].ny, inst[i].nz, inst[i].lo, inst[i].hi, inst[i].eps, inst[i].mu,
+                               precision, MX_FORM_LITERAL, stream);
+      if (st != MX_OK) return bail(st);
+      b->ctx.push_back(c);
+      b->h.push_back(inst[i].h);
+      st = mx_autotune(c);  // the pass schedules of this shape (cached per process; before any load)
+      if (st != MX_OK) return bail(st);
+      cudaStream_t ls = nullptr;
+      cudaEvent_t ev = nullptr;
+      if (cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking) != cudaSuccess) return bail(MX_E_CUDA);
+      b->lstreams.push_back(ls);
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return bail(MX_E_CUDA);
+      b->ldone.push_back(ev);
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return bail(MX_E_CUDA);
+    b->grec.assign(n, nullptr);
+    b->grec_cap.assign(n, 0);
+    *out = b;
+    return MX_OK;
+  }
   const unsigned ch = precision == MX_FP64 ? mx::bt_ch<double>() : mx::bt_ch<float>();
   unsigned long long chunks = 0, q = 0;
   for (int i = 0; i < n; ++i) {
@@ -189,6 +372,11 @@ mx_status mx_batch_step(mx_batch* b, long long nsteps, int invariants_every) {
   if (nsteps == 0) return MX_OK;
   for (int i = 0; i < b->n; ++i)
     if (!b->ctx[i]->loaded) return MX_E_STATE;
+  if (b->form == MX_FORM_LITERAL) {
+    const mx_status st = step_literal(b, nsteps, invariants_every);
+    if (st != MX_OK && st != MX_E_INVAL && st != MX_E_STATE) b->err = st;
+    return st;
+  }
   // the pinned descriptors may still be read by the previous launch's copy node
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(b, cudaErrorUnknown);
   // per-call descriptor fields; record capacity
@@ -253,6 +441,16 @@ mx_status mx_batch_sync(mx_batch* b) {
   if (!b) return MX_E_INVAL;
   if (b->err != MX_OK) return b->err;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(b, cudaErrorUnknown);
+  if (b->form == MX_FORM_LITERAL) {
+    for (int i = 0; i < b->n; ++i) {
+      const mx_status st = mx_sync(b->ctx[i]);  // latched errors and timed-out waits of the instance
+      if (st != MX_OK) {
+        b->err = st;
+        return st;
+      }
+    }
+    return MX_OK;
+  }
   unsigned flags[3] = {0, 0, 0};
   if (cudaMemcpy(flags, b->bar, sizeof(flags), cudaMemcpyDeviceToHost) != cudaSuccess) return fail(b, cudaErrorUnknown);
   if (flags[2]) {
@@ -264,7 +462,7 @@ mx_status mx_batch_sync(mx_batch* b) {
 
 mx_status mx_batch_graph_used(mx_batch* b, int* used) {
   if (!b || !used) return MX_E_INVAL;
-  *used = b->graph_err ? -b->graph_err : (b->use_graph && !b->graphs.empty());
+  *used = b->graph_err ? -b->graph_err : (b->use_graph && (!b->graphs.empty() || !b->lgraphs.empty()));
   return MX_OK;
 }
 
@@ -272,6 +470,12 @@ void mx_batch_destroy(mx_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : b->lgraphs) cudaGraphExecDestroy(kv.second);
+  for (cudaStream_t ls : b->lstreams) cudaStreamDestroy(ls);
+  for (cudaEvent_t ev : b->ldone) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (double* r : b->grec)
+    if (r) cudaFree(r);
   for (mx_ctx* c : b->ctx) mx_destroy(c);
   if (b->h_inst) cudaFreeHost(b->h_inst);
   if (b->d_inst) cudaFree(b->d_inst);

@@ -35,7 +35,7 @@ using Clock = std::chrono::steady_clock;
 struct Req {
   long long id;
   mx_request r;
-  Clock::time_point t_submit, t_done;
+  Clock::time_point t_submit, t_admit, t_done;
   int state = 0;  // 0 queued, 1 running, 2 done, < 0 failed (-status)
   mx_ctx* ctx = nullptr;
   cudaEvent_t done_ev = nullptr;
@@ -79,6 +79,10 @@ struct mx_server {
   size_t in_use = 0, high_water = 0;
   long long next_id = 1;
   long long admitted = 0, completed = 0, rejected = 0;
+  // device concurrency: time-weighted count of admitted, unfinished requests
+  Clock::time_point last_change = Clock::now();
+  double busy_s = 0.0, conc_area = 0.0, request_s_sum = 0.0;
+  long long max_conc = 0;
   bool stop = false;
   int device = 0;
   std::thread worker;
@@ -172,8 +176,20 @@ mx_status launch_request(Req* q) {
   return MX_OK;
 }
 
+// Before the active set changes: add the time since the last change, weighted by its size.
+void account(mx_server* s) {
+  const Clock::time_point now = Clock::now();
+  const double dt = std::chrono::duration<double>(now - s->last_change).count();
+  if (!s->active.empty()) {
+    s->busy_s += dt;
+    s->conc_area += dt * (double)s->active.size();
+  }
+  s->last_change = now;
+}
+
 void finish_request(mx_server* s, Req* q, mx_status st) {
   q->t_done = Clock::now();
+  if (q->state == 1) s->request_s_sum += std::chrono::duration<double>(q->t_done - q->t_admit).count();
   if (st == MX_OK && q->ctx) {
     long long nrec = 0;
     st = mx_read_invariants(q->ctx, nullptr, 0, &nrec);
@@ -221,6 +237,7 @@ void worker_loop(mx_server* s) {
       s->queue.pop_front();
       q->ctx = c;
       q->state = 1;
+      q->t_admit = Clock::now();
       ++s->admitted;
       const mx_status st = launch_request(q);
       if (st != MX_OK) {
@@ -228,7 +245,9 @@ void worker_loop(mx_server* s) {
         s->cv_done.notify_all();
         continue;
       }
+      account(s);
       s->active.push_back(q);
+      s->max_conc = std::max(s->max_conc, (long long)s->active.size());
     }
     // complete
     bool any = false;
@@ -240,6 +259,7 @@ void worker_loop(mx_server* s) {
         continue;
       }
       finish_request(s, q, e == cudaSuccess ? mx_sync(q->ctx) : MX_E_CUDA);
+      account(s);
       s->active.erase(s->active.begin() + (long)i);
       any = true;
     }
@@ -349,6 +369,10 @@ mx_status mx_server_stats(mx_server* s, mx_server_info* out) {
   out->hbm_high_water = s->high_water;
   out->hbm_budget = s->budget;
   out->pooled_contexts = (long long)s->idle.size();
+  out->max_concurrent = s->max_conc;
+  out->busy_s = s->busy_s;
+  out->mean_concurrent = s->busy_s > 0.0 ? s->conc_area / s->busy_s : 0.0;
+  out->request_s_sum = s->request_s_sum;
   return MX_OK;
 }
 

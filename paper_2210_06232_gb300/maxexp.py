@@ -40,7 +40,8 @@ class mx_server_info(C.Structure):
     _fields_ = [("submitted", C.c_longlong), ("admitted", C.c_longlong), ("completed", C.c_longlong),
                 ("rejected", C.c_longlong), ("queued", C.c_longlong), ("active", C.c_longlong),
                 ("pooled_contexts", C.c_longlong), ("hbm_in_use", C.c_size_t), ("hbm_high_water", C.c_size_t),
-                ("hbm_budget", C.c_size_t)]
+                ("hbm_budget", C.c_size_t), ("max_concurrent", C.c_longlong), ("mean_concurrent", C.c_double),
+                ("busy_s", C.c_double), ("request_s_sum", C.c_double)]
 
 
 class mx_invariants(C.Structure):
@@ -89,6 +90,7 @@ def _load():
         "mx_server_stats": (I, [P, C.POINTER(mx_server_info)]),
         "mx_server_destroy": (None, [P]),
         "mx_batch_create": (I, [C.POINTER(P), C.POINTER(mx_instance_desc), I, I, V]),
+        "mx_batch_create_form": (I, [C.POINTER(P), C.POINTER(mx_instance_desc), I, I, I, V]),
         "mx_batch_size": (I, [P, C.POINTER(I)]),
         "mx_batch_instance": (I, [P, I, C.POINTER(P)]),
         "mx_batch_load_random": (I, [P, C.c_ulonglong, D]),
@@ -138,6 +140,7 @@ mx_server_result = _lib.mx_server_result
 mx_server_stats = _lib.mx_server_stats
 mx_server_destroy = _lib.mx_server_destroy
 mx_batch_create = _lib.mx_batch_create
+mx_batch_create_form = _lib.mx_batch_create_form
 mx_batch_size = _lib.mx_batch_size
 mx_batch_instance = _lib.mx_batch_instance
 mx_batch_load_random = _lib.mx_batch_load_random
@@ -319,11 +322,11 @@ class Solver:
 class _Borrowed(Solver):
     """A context owned by a batch: same methods as Solver, never destroyed here."""
 
-    def __init__(self, handle, n, precision):
+    def __init__(self, handle, n, precision, form=MX_FORM_SPECTRAL):
         self._h = handle
         self.n = n
         self.precision = precision
-        self.form = MX_FORM_SPECTRAL
+        self.form = form
         self.dtype = np.float64 if precision == MX_FP64 else np.float32
 
     def close(self):
@@ -333,8 +336,9 @@ class _Borrowed(Solver):
 class Batch:
     """Independent spectral-form instances advanced by one persistent launch per step call."""
 
-    def __init__(self, instances, precision=MX_FP32, stream=None):
-        """instances: list of dicts with keys n=(nx,ny,nz), lo, hi, eps, mu, h."""
+    def __init__(self, instances, precision=MX_FP32, stream=None, form=MX_FORM_SPECTRAL):
+        """instances: list of dicts with keys n=(nx,ny,nz), lo, hi, eps, mu, h; form MX_FORM_SPECTRAL
+        (one persistent launch per step call) or MX_FORM_LITERAL (graph of per-instance pass chains)."""
         arr = (mx_instance_desc * len(instances))()
         for i, d in enumerate(instances):
             arr[i].nx, arr[i].ny, arr[i].nz = (int(v) for v in d["n"])
@@ -343,9 +347,10 @@ class Batch:
             arr[i].eps, arr[i].mu, arr[i].h = float(d["eps"]), float(d["mu"]), float(d["h"])
         h = C.c_void_p()
         s = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
-        check(mx_batch_create(C.byref(h), arr, len(instances), int(precision), s), "mx_batch_create")
+        check(mx_batch_create_form(C.byref(h), arr, len(instances), int(precision), int(form), s), "mx_batch_create")
         self._h = h
         self.precision = precision
+        self.form = form
         self.specs = [dict(d) for d in instances]
 
     def __len__(self):
@@ -354,7 +359,7 @@ class Batch:
     def instance(self, i):
         c = C.c_void_p()
         check(mx_batch_instance(self._h, int(i), C.byref(c)), "mx_batch_instance")
-        return _Borrowed(c, tuple(int(v) for v in self.specs[i]["n"]), self.precision)
+        return _Borrowed(c, tuple(int(v) for v in self.specs[i]["n"]), self.precision, self.form)
 
     def load_random(self, seed, sigma):
         check(mx_batch_load_random(self._h, int(seed), float(sigma)), "mx_batch_load_random")

@@ -133,3 +133,67 @@ def test_batch_matches_oracle_per_field(prec):
         sc = inv_scales(r0, sp["eps"], sp["mu"])
         assert inv_diff(inv[-1], rn, sc) < tol
     b.close()
+
+
+def _run_literal_batch(mx, specs, prec, inits, steps, every, calls=2):
+    import torch
+
+    b = mx.Batch(specs, prec, form=mx.MX_FORM_LITERAL)
+    npdt = np.float64 if prec == mx.MX_FP64 else np.float32
+    for i, (E0, H0) in enumerate(inits):
+        b.instance(i).load(E0.astype(npdt), H0.astype(npdt))
+    for _ in range(calls):
+        b.step(steps, every)  # the second call replays the captured graph
+    b.sync()
+    out = []
+    for i in range(len(specs)):
+        inst = b.instance(i)
+        E, H = inst.read_numpy()
+        out.append((E.astype(np.float64), H.astype(np.float64), inst.invariants(), inst.time()))
+    used = b.graph_used()
+    b.close()
+    return out, used
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_literal_batch_alone_equals_in_mix_and_matches_oracle(prec):
+    """Literal-form batch (every instance's x, y, fused z, y, x passes as parallel graph branches, with
+    its shape's autotuned schedules): bit-identical alone and in the mix, each of the six fields
+    against the oracle's literal stepping (Alg. 1 + Alg. 2 with t_end = h, repeated) within 1e-12
+    (FP64) or 1e-5 (FP32), invariants of the last record against the oracle's."""
+    from oracle import invariants as oinv
+
+    mx = solver_mod()
+    P = mx.MX_FP64 if prec == "fp64" else mx.MX_FP32
+    npdt = np.float64 if prec == "fp64" else np.float32
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    specs = [SPECS[3], SPECS[4], dict(n=(16, 12, 32), eps=1.7, mu=0.6, h=0.043), dict(n=(20, 24, 80), eps=2.2, mu=1.4, h=0.03)]
+    inits = []
+    for i, sp in enumerate(specs):
+        g = synth.Grid(sp["n"], sp.get("lo", (0, 0, 0)), sp.get("hi", (TWO_PI,) * 3))
+        rng = np.random.default_rng(60 + i)
+        inits.append((rng.standard_normal((3,) + g.shape).astype(npdt).astype(np.float64),
+                      rng.standard_normal((3,) + g.shape).astype(npdt).astype(np.float64)))
+    steps, every = 3, 1
+    mix, used = _run_literal_batch(mx, specs, P, inits, steps, every)
+    assert used == 1, f"graph capture refused: CUDA error {-used}"
+    for i, sp in enumerate(specs):
+        alone, _ = _run_literal_batch(mx, [sp], P, [inits[i]], steps, every)
+        np.testing.assert_array_equal(mix[i][0], alone[0][0])
+        np.testing.assert_array_equal(mix[i][1], alone[0][1])
+        assert len(mix[i][2]) == len(alone[0][2]) == 1 + 2 * steps
+        for ra, rb in zip(mix[i][2], alone[0][2]):
+            for k in ra:
+                np.testing.assert_array_equal(ra[k], rb[k])
+        t, nstep = mix[i][3]
+        assert nstep == 2 * steps and abs(t - 2 * steps * sp["h"]) < 1e-12
+        g = synth.Grid(sp["n"], sp.get("lo", (0, 0, 0)), sp.get("hi", (TWO_PI,) * 3))
+        E0, H0 = inits[i]
+        Eo, Ho = scheme.step(E0, H0, g.lo, g.hi, sp["eps"], sp["mu"], sp["h"], 2 * steps)
+        errs = field_rel_l2(mix[i][0], mix[i][1], Eo, Ho)
+        assert max(errs) < tol, (i, errs)
+        r0 = oinv.invariants(E0, H0, g.lo, g.hi, sp["eps"], sp["mu"])
+        rn = oinv.invariants(Eo, Ho, g.lo, g.hi, sp["eps"], sp["mu"])
+        sc = inv_scales(r0, sp["eps"], sp["mu"])
+        assert [r["step"] for r in mix[i][2]] == list(range(2 * steps + 1))
+        assert inv_diff(mix[i][2][-1], rn, sc) < tol
