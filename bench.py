@@ -339,6 +339,7 @@ def batch_run(torch, mx, peak, steps, warmup, stream, ninst=64, seed=4, form=Non
         e = [r["E1"] for r in inv]
         drift = max(drift, (max(e) - min(e)) / e[0])
     used = b.graph_used()
+    shape = b.launch_shape()
     b.close()
     min_bytes = 12 * pts * 4
     return {
@@ -350,7 +351,8 @@ def batch_run(torch, mx, peak, steps, warmup, stream, ninst=64, seed=4, form=Non
         "instances": ninst,
         "field_points": pts,
         "shapes": {"x".join(map(str, sh)): sum(1 for sp in specs if tuple(sp["n"]) == sh) for sh in BATCH_SHAPES},
-        "launches_per_call": 1,
+        "launches_per_call": 1 if form != mx.MX_FORM_LITERAL else None,
+        "persistent_launch": {"blocks": shape[0], "threads_per_block": shape[1]} if shape[0] else None,
         "graph_replayed": used,
         "step_hbm_roofline_frac": (min_bytes / (ms / steps / 1e3) / 1e9) / peak,
         "energy_rel_drift_max": drift,

@@ -240,6 +240,9 @@ mx_status mx_batch_sync(mx_batch* b);
  * launched directly).  A batch created with a NULL stream uses a stream of
  * its own (the legacy default stream cannot be captured). */
 mx_status mx_batch_graph_used(mx_batch* b, int* used);
+/* Blocks and threads per block of the spectral form's persistent launch (0, 0 for the literal
+ * form, which launches each instance's passes). */
+mx_status mx_batch_launch_shape(mx_batch* b, int* blocks, int* threads);
 void mx_batch_destroy(mx_batch* b);
 
 /*

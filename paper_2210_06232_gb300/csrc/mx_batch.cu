@@ -460,6 +460,13 @@ mx_status mx_batch_sync(mx_batch* b) {
   return MX_OK;
 }
 
+mx_status mx_batch_launch_shape(mx_batch* b, int* blocks, int* threads) {
+  if (!b || !blocks || !threads) return MX_E_INVAL;
+  *blocks = b->form == MX_FORM_LITERAL ? 0 : b->grid;
+  *threads = b->form == MX_FORM_LITERAL ? 0 : mx::BT_THREADS;
+  return MX_OK;
+}
+
 mx_status mx_batch_graph_used(mx_batch* b, int* used) {
   if (!b || !used) return MX_E_INVAL;
   *used = b->graph_err ? -b->graph_err : (b->use_graph && (!b->graphs.empty() || !b->lgraphs.empty()));

@@ -213,7 +213,10 @@ __device__ void batch_final(const BatchArgs& a, long long step_local, const doub
 }
 
 template <typename T>
-__global__ void __maxnreg__(112) k_batch_steps(BatchArgs a) {  // 2 blocks of BT_THREADS per SM
+// 112 registers: one block of BT_THREADS per SM (nine warps: five on one SM sub-partition would
+// need at most 102 registers each for two blocks).  Measured at 64 uneven instances: 0.83 ms per
+// step with one block per SM, 0.87 ms with two blocks at 96 registers (spills).
+__global__ void __maxnreg__(112) k_batch_steps(BatchArgs a) {
   using C = cx<T>;
   constexpr int PPT = BTraits<T>::PPT;
   constexpr int CH = bt_ch<T>();

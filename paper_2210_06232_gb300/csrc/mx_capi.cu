@@ -72,16 +72,19 @@ mx_status cuda_fail(mx_ctx* c, cudaError_t e) {
     }                                                          \
   } while (0)
 
-// exp(-2 pi i j / n) for j < n, reduced to the first quadrant exactly when 4 | n.
-void twiddles(int n, std::vector<double>& re, std::vector<double>& im) {
+// exp(-2 pi i j / n) for j < n in long double (at least 64-bit significands: the FP64 tables keep
+// hi + lo pairs), reduced to the first quadrant exactly when 4 | n.
+using ldvec = std::vector<long double>;
+void twiddles(int n, ldvec& re, ldvec& im) {
+  const long double PI = 3.141592653589793238462643383279502884L;
   re.resize(n);
   im.resize(n);
   for (int j = 0; j < n; ++j) {
-    double c, s;
+    long double c, s;
     if (n % 4 == 0) {
       const int q = (4 * j) / n, r = 4 * j - q * n;  // angle = (q + r/n) * pi/2
-      const double a = (M_PI / 2.0) * ((double)r / (double)n);
-      const double ca = cos(a), sa = sin(a);
+      const long double a = (PI / 2.0L) * ((long double)r / (long double)n);
+      const long double ca = cosl(a), sa = sinl(a);
       switch (q) {
         case 0: c = ca; s = sa; break;
         case 1: c = -sa; s = ca; break;
@@ -89,9 +92,9 @@ void twiddles(int n, std::vector<double>& re, std::vector<double>& im) {
         default: c = sa; s = -ca; break;
       }
     } else {
-      const double a = 2.0 * M_PI * (double)j / (double)n;
-      c = cos(a);
-      s = sin(a);
+      const long double a = 2.0L * PI * (long double)j / (long double)n;
+      c = cosl(a);
+      s = sinl(a);
     }
     re[j] = c;
     im[j] = -s;
@@ -100,8 +103,8 @@ void twiddles(int n, std::vector<double>& re, std::vector<double>& im) {
 
 // Appends the stage-major twiddle table of the length-n line FFT with E values per
 // thread (mx::tw_stage_off): stage (NS, R), entry [r-1][k] = exp(-2 pi i r k / (NS R)).
-void stage_twiddles(int n, int E, std::vector<double>& re, std::vector<double>& im) {
-  std::vector<double> wr, wi;
+void stage_twiddles(int n, int E, ldvec& re, ldvec& im) {
+  ldvec wr, wi;
   twiddles(n, wr, wi);
   for (int ns = 1; ns < n;) {
     const int r = mx::pick_radix(n / ns, E);
@@ -123,12 +126,12 @@ void stage_twiddles(int n, int E, std::vector<double>& re, std::vector<double>& 
 //   y: the stage table of the ny-point FFT;
 //   z: the stage table of the nz-point FFT, then that of the fused z pass's plan
 //     (starting at entry *zf_off).
-void axis_twiddles(int axis, int n, bool fp64, std::vector<double>& re, std::vector<double>& im, int* zf_off) {
+void axis_twiddles(int axis, int n, bool fp64, ldvec& re, ldvec& im, int* zf_off) {
   re.clear();
   im.clear();
   if (axis == 0) {
     const int M = n / 2;
-    std::vector<double> wr, wi;
+    ldvec wr, wi;
     twiddles(n, wr, wi);
     re.assign(wr.begin(), wr.begin() + M);
     im.assign(wi.begin(), wi.begin() + M);
@@ -143,22 +146,25 @@ void axis_twiddles(int axis, int n, bool fp64, std::vector<double>& re, std::vec
   }
 }
 
-// FP64: double2 per entry.  FP32: float4 (hi.x, hi.y, lo.x, lo.y) with value = hi + lo, except the
-// fused z pass's lifting constants.
+// Entries hi + lo in the arithmetic type: FP64 dd2 (hi.x, hi.y, lo.x, lo.y), FP32 float4 the same,
+// except the FP32 fused z pass's lifting constants.
 cudaError_t upload_twiddles(mx_ctx* c, int axis, int n, void** dst) {
-  std::vector<double> re, im;
+  ldvec re, im;
   int zf_off = 0;
   axis_twiddles(axis, n, c->prec == MX_FP64, re, im, &zf_off);
   if (axis == 2) c->twz_zf = zf_off;
   n = std::max<int>(1, (int)re.size());
-  re.resize(n, 1.0);
-  im.resize(n, 0.0);
+  re.resize(n, 1.0L);
+  im.resize(n, 0.0L);
   if (c->prec == MX_FP64) {
-    cudaError_t e = mx::dev_alloc(dst, (size_t)n * sizeof(double2));
+    cudaError_t e = mx::dev_alloc(dst, (size_t)n * sizeof(mx::dd2));
     if (e != cudaSuccess) return e;
-    std::vector<double2> h(n);
-    for (int j = 0; j < n; ++j) h[j] = make_double2(re[j], im[j]);
-    return cudaMemcpy(*dst, h.data(), n * sizeof(double2), cudaMemcpyHostToDevice);
+    std::vector<mx::dd2> h(n);
+    for (int j = 0; j < n; ++j) {
+      const double rh = (double)re[j], ih = (double)im[j];
+      h[j] = mx::dd2{rh, ih, (double)(re[j] - (long double)rh), (double)(im[j] - (long double)ih)};
+    }
+    return cudaMemcpy(*dst, h.data(), n * sizeof(mx::dd2), cudaMemcpyHostToDevice);
   }
   cudaError_t e = mx::dev_alloc(dst, (size_t)n * sizeof(float4));
   if (e != cudaSuccess) return e;
@@ -169,14 +175,16 @@ cudaError_t upload_twiddles(mx_ctx* c, int axis, int n, void** dst) {
   const int lift_from = axis == 2 ? c->twz_zf : n;
   for (int j = 0; j < n; ++j) {
     if (j >= lift_from && (int)re.size() > lift_from) {
-      double a = atan2(im[j], re[j]), sg = 1.0;
-      if (a > M_PI / 2) a -= M_PI, sg = -1.0;
-      else if (a < -M_PI / 2) a += M_PI, sg = -1.0;
-      h[j] = make_float4((float)(-tan(0.5 * a)), (float)sin(a), (float)sg, 0.f);
+      const long double PI = 3.141592653589793238462643383279502884L;
+      long double a = atan2l(im[j], re[j]);
+      float sg = 1.f;
+      if (a > PI / 2) a -= PI, sg = -1.f;
+      else if (a < -PI / 2) a += PI, sg = -1.f;
+      h[j] = make_float4((float)(-tanl(0.5L * a)), (float)sinl(a), sg, 0.f);
       continue;
     }
     const float rh = (float)re[j], ih = (float)im[j];
-    h[j] = make_float4(rh, ih, (float)(re[j] - (double)rh), (float)(im[j] - (double)ih));
+    h[j] = make_float4(rh, ih, (float)(re[j] - (long double)rh), (float)(im[j] - (long double)ih));
   }
   return cudaMemcpy(*dst, h.data(), n * sizeof(float4), cudaMemcpyHostToDevice);
 }

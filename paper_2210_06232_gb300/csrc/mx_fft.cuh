@@ -24,20 +24,23 @@ template <> struct vec2<float> { using type = float2; };
 template <> struct vec2<double> { using type = double2; };
 template <typename T> using cx = typename vec2<T>::type;
 
-// Twiddle storage: FP64 keeps one double2; FP32 keeps the value as a pair
-// hi + lo of floats (float4: hi.x, hi.y, lo.x, lo.y).  In FP32 every FFT
+// Twiddle storage: the value as a pair hi + lo in the arithmetic type (FP32:
+// float4 hi.x, hi.y, lo.x, lo.y; FP64: the same in doubles).  Every FFT
 // constant is applied as hi + lo: a rounded constant would scale each
 // frequency by the same wrong factor on every transform, and in a repeated
 // forward/inverse loop that bias grows linearly with the step count.
+struct __align__(16) dd2 { double x, y, z, w; };  // hi.x, hi.y, lo.x, lo.y
 template <typename T> struct tw_t;
 template <> struct tw_t<float> { using type = float4; };
-template <> struct tw_t<double> { using type = double2; };
+template <> struct tw_t<double> { using type = dd2; };
 template <typename T> using twv = typename tw_t<T>::type;
 
 // a * w (forward, DIR < 0) or a * conj(w) (inverse)
-template <int DIR> __device__ __forceinline__ double2 twmul(double2 a, double2 w) {
-  const double wy = DIR < 0 ? w.y : -w.y;
-  return double2{a.x * w.x - a.y * wy, a.x * wy + a.y * w.x};
+template <int DIR> __device__ __forceinline__ double2 twmul(double2 a, dd2 w) {
+  const double hy = DIR < 0 ? w.y : -w.y, ly = DIR < 0 ? w.w : -w.w;
+  const double re = fma(a.x, w.x, fma(-a.y, hy, a.x * w.z - a.y * ly));
+  const double im = fma(a.x, hy, fma(a.y, w.x, a.x * ly + a.y * w.z));
+  return double2{re, im};
 }
 template <int DIR> __device__ __forceinline__ float2 twmul(float2 a, float4 w) {
   const float hy = DIR < 0 ? w.y : -w.y, ly = DIR < 0 ? w.w : -w.w;
@@ -45,18 +48,28 @@ template <int DIR> __device__ __forceinline__ float2 twmul(float2 a, float4 w) {
   const float im = fmaf(a.x, hy, fmaf(a.y, w.x, a.x * ly + a.y * w.z));
   return float2{re, im};
 }
-// x * c for a real constant c given in FP64: hi + lo in FP32, plain in FP64
+// x * c for a real constant c given as a double-double hi + lo (or a double): applied as a
+// hi + lo pair of the arithmetic type
 template <typename T> struct KC;
 template <> struct KC<double> {
-  double v;
-  __device__ __forceinline__ constexpr KC(double c) : v(c) {}
-  __device__ __forceinline__ double mul(double x) const { return x * v; }
+  double h, l;
+  __device__ __forceinline__ constexpr KC(double c) : h(c), l(0.0) {}
+  __device__ __forceinline__ constexpr KC(double hi, double lo) : h(hi), l(lo) {}
+  __device__ __forceinline__ double mul(double x) const { return fma(x, h, x * l); }
 };
 template <> struct KC<float> {
   float h, l;
   __device__ __forceinline__ constexpr KC(double c) : h((float)c), l((float)(c - (double)(float)c)) {}
+  __device__ __forceinline__ constexpr KC(double hi, double lo) : h((float)hi), l((float)((hi - (double)(float)hi) + lo)) {}
   __device__ __forceinline__ float mul(float x) const { return fmaf(x, h, x * l); }
 };
+// Butterfly constants as double-double pairs (hi = the double nearest, lo = the rest).
+#define MX_KC_INV_SQRT2 0.7071067811865476, -4.833646656726457e-17
+#define MX_KC_SIN_2PI_3 0.8660254037844386, 5.0175421109034514e-17
+#define MX_KC_COS_2PI_5 0.30901699437494745, -2.716057601841253e-17
+#define MX_KC_COS_4PI_5 -0.8090169943749475, 2.716057601841253e-17
+#define MX_KC_SIN_2PI_5 0.9510565162951535, 4.0934500900087295e-17
+#define MX_KC_SIN_4PI_5 0.5877852522924731, -7.93475083819002e-18
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
@@ -90,7 +103,7 @@ template <int DIR, int S, typename C> __device__ __forceinline__ void bfly4(C* v
 
 template <int DIR, int S, typename C> __device__ __forceinline__ void bfly8(C* v) {
   using T = decltype(v[0].x);
-  constexpr KC<T> h(0.70710678118654752440);  // 1/sqrt(2)
+  constexpr KC<T> h(MX_KC_INV_SQRT2);  // 1/sqrt(2)
   C e[4] = {v[0], v[2 * S], v[4 * S], v[6 * S]};
   C o[4] = {v[S], v[3 * S], v[5 * S], v[7 * S]};
   bfly4<DIR, 1>(e);
@@ -110,7 +123,7 @@ template <int DIR, int S, typename C> __device__ __forceinline__ void bfly8(C* v
 template <int DIR, int S, typename C> __device__ __forceinline__ void bfly3(C* v) {
   using T = decltype(v[0].x);
   const T c1 = (T)-0.5;                        // cos 2 pi/3 (exact)
-  constexpr KC<T> s1(0.86602540378443864676);  // sin 2 pi/3
+  constexpr KC<T> s1(MX_KC_SIN_2PI_3);  // sin 2 pi/3
   C a = v[0], b = v[S], c = v[2 * S];
   C s = cadd(b, c), d = csub(b, c);
   C t = C{a.x + c1 * s.x, a.y + c1 * s.y};
@@ -122,8 +135,8 @@ template <int DIR, int S, typename C> __device__ __forceinline__ void bfly3(C* v
 
 template <int DIR, int S, typename C> __device__ __forceinline__ void bfly5(C* v) {
   using T = decltype(v[0].x);
-  constexpr KC<T> c1(0.30901699437494742410), c2(-0.80901699437494742410);  // cos 2pi/5, cos 4pi/5
-  constexpr KC<T> s1(0.95105651629515357212), s2(0.58778525229247312917);   // sin 2pi/5, sin 4pi/5
+  constexpr KC<T> c1(MX_KC_COS_2PI_5), c2(MX_KC_COS_4PI_5);  // cos 2pi/5, cos 4pi/5
+  constexpr KC<T> s1(MX_KC_SIN_2PI_5), s2(MX_KC_SIN_4PI_5);  // sin 2pi/5, sin 4pi/5
   C a = v[0], b = v[S], c = v[2 * S], d = v[3 * S], e = v[4 * S];
   C p1 = cadd(b, e), m1 = csub(b, e), p2 = cadd(c, d), m2 = csub(c, d);
   C t1 = C{a.x + c1.mul(p1.x) + c2.mul(p2.x), a.y + c1.mul(p1.y) + c2.mul(p2.y)};

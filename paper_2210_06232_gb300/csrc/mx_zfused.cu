@@ -38,7 +38,7 @@ cudaError_t launch_z_fused<float>(int coef_kind, float2* data, const GridParams&
 
 template <>
 cudaError_t launch_z_fused<double>(int coef_kind, double2* data, const GridParams& g, const void* tab, double t,
-                                   const double2* tw, int grid, bool pipelined, double* partials, unsigned* counter, double* record,
+                                   const dd2* tw, int grid, bool pipelined, double* partials, unsigned* counter, double* record,
                                    cudaStream_t s) {
   if (coef_kind == 0) return zf_dispatch<double, Coef<double>>(data, g, tab, t, tw, grid, pipelined, partials, counter, record, s);
   if (coef_kind == 2) return zf_dispatch<double, Coef<double>>(data, g, nullptr, t, tw, grid, pipelined, partials, counter, record, s);

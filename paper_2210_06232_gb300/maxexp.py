@@ -97,6 +97,7 @@ def _load():
         "mx_batch_step": (I, [P, LL, I]),
         "mx_batch_sync": (I, [P]),
         "mx_batch_graph_used": (I, [P, C.POINTER(I)]),
+        "mx_batch_launch_shape": (I, [P, C.POINTER(I), C.POINTER(I)]),
         "mx_batch_destroy": (None, [P]),
         "mx_schedule": (I, [P, C.POINTER(I), I]),
         "mx_set_schedule": (I, [P, C.POINTER(I), I]),
@@ -147,6 +148,7 @@ mx_batch_load_random = _lib.mx_batch_load_random
 mx_batch_step = _lib.mx_batch_step
 mx_batch_sync = _lib.mx_batch_sync
 mx_batch_graph_used = _lib.mx_batch_graph_used
+mx_batch_launch_shape = _lib.mx_batch_launch_shape
 mx_batch_destroy = _lib.mx_batch_destroy
 mx_schedule = _lib.mx_schedule
 mx_set_schedule = _lib.mx_set_schedule
@@ -375,6 +377,12 @@ class Batch:
         v = C.c_int(0)
         check(mx_batch_graph_used(self._h, C.byref(v)), "mx_batch_graph_used")
         return v.value
+
+    def launch_shape(self):
+        """(blocks, threads per block) of the spectral form's persistent launch; (0, 0) for the literal form."""
+        nb, nt = C.c_int(0), C.c_int(0)
+        check(mx_batch_launch_shape(self._h, C.byref(nb), C.byref(nt)), "mx_batch_launch_shape")
+        return nb.value, nt.value
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -40,12 +40,13 @@ def test_config2_full_size_fp64(form):
     assert rel_l2(Ed.cpu().numpy(), Hd.cpu().numpy(), Eo, Ho) < 1e-12
     assert len(inv) == n + 1
     sc = inv_scales(inv[0], eps, mu)
-    # The spectral form evaluates R(t_n) directly: no accumulation, 1e-13.  The literal form
-    # re-applies the same rounded R(h) n times, and its FP64 rounding accumulates about linearly
-    # (the FP64 oracle stepping literally on 64 x 128 x 64 drifts in E1 by 5.5e-14, 1.1e-13, 1.6e-13
-    # and 2.2e-13 after 250, 500, 750 and 1000 steps): bound 1e-13 + 4e-16 per step.
-    bound = 1e-13 if form == "spectral" else 1e-13 + 4e-16 * n
-    assert max(inv_diff(r, inv[0], sc) for r in inv) < bound
+    # 1e-13 relative drift in both forms.  The spectral form evaluates R(t_n) directly (nothing
+    # accumulates); the literal form re-applies the same transforms and R(h) every step, and keeps
+    # within the bound because every FFT constant is applied as a double-double hi + lo pair (with
+    # FP64-rounded constants it drifted 3.2e-13 over these 1000 steps).
+    drift = max(inv_diff(r, inv[0], sc) for r in inv)
+    print(form, "max normalised invariant drift over", n, "steps:", drift)
+    assert drift < 1e-13
 
 
 def _plane_wave_device(torch, n, params, dtype):

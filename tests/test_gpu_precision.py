@@ -58,11 +58,18 @@ def test_fp32_error_vs_fp64_oracle_256(case, form):
     s.sync()
     inv = s.invariants()
     s.close()
-    errs = _field_errors(Ef.double().cpu().numpy(), Hf.double().cpu().numpy(), Eo, Ho)
+    En, Hn = Ef.double().cpu().numpy(), Hf.double().cpu().numpy()
+    errs = _field_errors(En, Hn, Eo, Ho)
     print(form, "per-field rel L2", ["%.2e" % e for e in errs])
     e1 = [r["E1"] for r in inv]
     print(form, "E1 rel drift", (max(e1) - min(e1)) / e1[0])
     assert max(errs) <= 1e-5
+    # the FP32 path's invariant sums (FP32 per thread or warp, compensated, FP64 across warps and
+    # blocks) against the same sums in FP64 over the FP32 state it returned: E1 = (mu <H,H> + eps <E,E>)/2
+    e1_fp64 = 0.5 * (np.sum(Hn ** 2) + np.sum(En ** 2)) / float(np.prod(n))
+    acc = abs(inv[-1]["E1"] - e1_fp64) / e1_fp64
+    print(form, "E1 of the final state: FP32-path sums vs FP64 sums, rel", acc)
+    assert acc < 1e-6
 
 
 def test_fp64_spectral_256_matches_oracle(case):
