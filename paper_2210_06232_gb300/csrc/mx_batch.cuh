@@ -60,7 +60,7 @@ template <> struct BTraits<double> {
   static constexpr int PPT = 1;
 };
 constexpr int BT_NST = 4;
-constexpr int BT_CONSUMERS = 256;
+constexpr int BT_CONSUMERS = 224;  // seven consumer warps + the producer: two blocks of eight warps per SM
 constexpr int BT_THREADS = BT_CONSUMERS + 32;
 constexpr int BT_CWARPS = BT_CONSUMERS / 32;
 constexpr int BT_SEG = 256;  // chunk-warp partials per invariant segment
@@ -213,9 +213,9 @@ __device__ void batch_final(const BatchArgs& a, long long step_local, const doub
 }
 
 template <typename T>
-// 112 registers: one block of BT_THREADS per SM (nine warps: five on one SM sub-partition would
-// need at most 102 registers each for two blocks).  Measured at 64 uneven instances: 0.83 ms per
-// step with one block per SM, 0.87 ms with two blocks at 96 registers (spills).
+// 112 registers and eight warps per block: two blocks per SM (four warps on each SM sub-partition,
+// 4 x 32 x 112 of its 16384 registers).  With eight consumer warps (nine per block) only one block
+// fits: five warps on a sub-partition would need at most 102 registers each.
 __global__ void __maxnreg__(112) k_batch_steps(BatchArgs a) {
   using C = cx<T>;
   constexpr int PPT = BTraits<T>::PPT;
