@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--only", choices=["dft8", "batch"], default=None,
                     help="dft8: only the tensor-core DFT-as-GEMM evaluation; batch: only the batched form "
-                         "(config 4, spectral; --steps steps); one JSON line, for profiling")
+                         "(64 uneven FP32 instances, spectral form; --steps steps); one JSON line, for profiling")
     return ap.parse_args()
 
 

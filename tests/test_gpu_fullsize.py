@@ -1,6 +1,6 @@
 """Parity at the benchmark's full sizes.
 
-* Config 2: 128 x 256 x 128 on [0,2pi] x [0,4pi] x [0,2pi], FP64, eps = 2, mu = 1, random
+* 128 x 256 x 128 on [0,2pi] x [0,4pi] x [0,2pi], FP64, eps = 2, mu = 1, random
   divergence-free fields (sigma = 8), h = 0.05, 1000 steps, invariants every step:
   element by element against the oracle (one step of size 1000 h, equal to the repeated step
   to round-off by the group property).
@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("form", ["spectral", "literal"])
-def test_config2_full_size_fp64(form):
+def test_random_128x256x128_1000_steps_fp64(form):
     import torch
 
     mx = solver_mod()

@@ -88,7 +88,7 @@ def test_invariants_conserved_fp64(form):
     assert inv[0]["divE"] > 0.1  # non-divergence-free input: the conserved value is non-trivial
 
 
-def test_config1_plane_waves_fp64():
+def test_plane_waves_16cube_100_steps_fp64():
     """16^3 on [0,2pi]^3, eps = mu = 1, 4 plane waves, h = 0.01, 100 steps, invariants every step."""
     mx = _mx()
     g = synth.Grid((16, 16, 16))
