@@ -542,17 +542,20 @@ __global__ void __launch_bounds__((N / E) * TX) k_fft_strided(cx<T>* __restrict_
 // which are exactly the frequencies its forward transforms produce and its
 // inverse transforms consume (mx_fft.cuh).  One read and one write of the
 // spectrum replace three passes (z forward, update, z inverse).
-// With TMAP a tile arrives by tensor copy in an input stage; once read, the
-// stage first holds the tile's coefficient-table entries (cp.async, during
-// the forward transforms), then takes the next tile while the update and the
-// inverse transforms run; the results leave through an output stage and a
-// tensor store.  Components are then transformed in threes (ZTile::TRIP; pairs
-// where the buffers do not fit), which cuts the barriers and shares each
-// twiddle load: the forward transforms exchange through unpadded, row-swizzled
-// buffers at the end of the input stage (past the coefficients) and one right
-// after it; the inverse transforms through six in the output stage (idle until
-// their results are written, once the previous store has read it),
-// alternating between two triplets so that an exchange has a single barrier.  Invariants of the updated state are summed per thread in T
+// With TMAP a tile arrives by tensor copy in an input stage, in boxes of three
+// components; the results leave through an output stage and tensor stores.
+// Components are transformed in threes (ZTile::TRIP; pairs where the buffers do
+// not fit), which cuts the barriers and shares each twiddle load.  With
+// triplets, once the tile is read the upper half of the input stage takes the
+// next tile's upper boxes at once, its lower half holds the coefficient-table
+// entries of this tile (cp.async, during the forward transforms) and takes the
+// next tile's lower boxes after the update: the next tile's copies run during
+// the whole of this tile's work instead of the inverse transforms only.  Both
+// directions of transforms exchange through six unpadded, row-swizzled buffers
+// in the output stage (once the previous store has read it), alternating
+// between two triplets so that an exchange has a single barrier.  Without
+// triplets the stage holds the coefficients and a second exchange buffer, and
+// the next tile's copies are issued after the update.  Invariants of the updated state are summed per thread in T
 // over a tile, then per warp in a compensated (Kahan) pair of T in shared
 // memory, converted to FP64 at the end: no FP64 arithmetic in the loop, where
 // an FP64 instruction costs the pipe as much with one active lane as with 32.
@@ -561,6 +564,7 @@ struct ZTile {
   static constexpr int P = N / E;
   static constexpr int NZC = (N + 255) / 256;  // boxes of the tensor copy along z
   static constexpr int ZC = N / NZC;           // z rows per box
+  static constexpr int NB = 2 * NZC;           // boxes per tile: along z, then two halves of three components
   static constexpr size_t stage_bytes = (size_t)6 * N * TX * sizeof(cx<T>);
   static constexpr int NT = P * TX;  // threads
   static constexpr int NL = 1;       // components per exchange buffer of this size (pairs: see above)
@@ -573,15 +577,15 @@ struct ZTile {
   // depends on m_z^2 only, and the Nyquist plane has m_z = 0), shared by the threads that need it
   static constexpr int NA = N / 2;
   static constexpr size_t coef_bytes = (size_t)NA * TX * 32;
-  // components in threes: the forward transforms exchange through the last two buffers' worth of
-  // the input stage and one more right after it, the inverse ones through six in the output stage
-  static constexpr bool TRIP = XK <= 7 && N % (XK + 1) == 0 && coef_bytes + 2 * xbuf_bytes <= stage_bytes &&
+  // components in threes: both directions exchange through six buffers in the output stage, the
+  // coefficients fill (part of) the input stage's lower half
+  static constexpr bool TRIP = XK <= 7 && N % (XK + 1) == 0 && 2 * coef_bytes <= stage_bytes &&
                                6 * xbuf_bytes <= stage_bytes;
-  static constexpr size_t smem_tma = TRIP ? 2 * stage_bytes + xbuf_bytes + tw_bytes + 16
-                                          : 2 * stage_bytes + tw_bytes + exch_bytes + 16;
+  static constexpr size_t smem_tma = TRIP ? 2 * stage_bytes + tw_bytes + 16 : 2 * stage_bytes + tw_bytes + exch_bytes + 16;
   // static shared memory of the kernel: compensated sums and the block reduction
   static constexpr size_t static_bytes = (size_t)2 * 32 * NSUM * sizeof(T) + (size_t)32 * NSUM * sizeof(double) + 128;
-  // element (comp c, z, column x) of the stage: box z / ZC, laid out [c][z % ZC][x]
+  // element (comp c, z, column x) of the stage: z box z / ZC, laid out [c][z % ZC][x] (the box of
+  // components c / 3 and z box b is the (2 b + c / 3)-th NB-th of the stage)
   __device__ __forceinline__ static int stage_index(int c, int z, int x) {
     return (z / ZC) * (6 * ZC * TX) + (c * ZC + z % ZC) * TX + x;
   }
@@ -594,23 +598,24 @@ __device__ __forceinline__ void z_tile_store(const void* tmap, const cx<T>* osta
   const int y = (int)((unsigned)tile / (unsigned)ntx);
   const int x0 = (int)((unsigned)tile - (unsigned)y * (unsigned)ntx) * TX;
 #pragma unroll
-  for (int h = 0; h < ZT::NZC; ++h)
-    tma_store_4d(tmap, reinterpret_cast<const unsigned char*>(ostage) + h * (ZT::stage_bytes / ZT::NZC), 2 * x0, y,
-                 h * ZT::ZC, 0);
+  for (int b = 0; b < ZT::NB; ++b)
+    tma_store_4d(tmap, reinterpret_cast<const unsigned char*>(ostage) + b * (ZT::stage_bytes / ZT::NB), 2 * x0, y,
+                 (b >> 1) * ZT::ZC, 3 * (b & 1));
   bulk_commit();
 }
 
-// Thread 0: the tensor copies of tile `tile` into the stage, completing on `full`.
-template <typename T, int N, int E, int TX>
+// Thread 0: tensor copies of boxes B0 .. B1 - 1 of tile `tile` into the stage, completing on `full`
+// (EXPECT: announce the whole tile's bytes, with the first copies of the tile).
+template <typename T, int N, int E, int TX, int B0 = 0, int B1 = ZTile<T, N, E, TX>::NB, bool EXPECT = true>
 __device__ __forceinline__ void z_tile_copy(const void* tmap, cx<T>* stage, uint64_t* full, long tile, int ntx) {
   using ZT = ZTile<T, N, E, TX>;
   const int y = (int)((unsigned)tile / (unsigned)ntx);
   const int x0 = (int)((unsigned)tile - (unsigned)y * (unsigned)ntx) * TX;
-  mbar_expect_tx(full, (uint32_t)ZT::stage_bytes);
+  if constexpr (EXPECT) mbar_expect_tx(full, (uint32_t)ZT::stage_bytes);
 #pragma unroll
-  for (int h = 0; h < ZT::NZC; ++h)
-    tma_load_4d(reinterpret_cast<unsigned char*>(stage) + h * (ZT::stage_bytes / ZT::NZC), tmap, 2 * x0, y, h * ZT::ZC, 0,
-                full);
+  for (int b = B0; b < B1; ++b)
+    tma_load_4d(reinterpret_cast<unsigned char*>(stage) + b * (ZT::stage_bytes / ZT::NB), tmap, 2 * x0, y,
+                (b >> 1) * ZT::ZC, 3 * (b & 1), full);
 }
 
 // Forward and inverse z transforms of NL components in the fused pass: in FP32 the exactly
@@ -645,16 +650,14 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
   constexpr int LS = strided_rows(N) * TX;  // exchange buffer of one component (TX lines side by side)
   extern __shared__ __align__(128) unsigned char zsmraw[];
   // [input stage, output stage (TMAP only)][twiddles][exchange buffer][mbarrier]; the stages also
-  // serve as second exchange buffers.  Triplets: [input stage][exchange buffer][output stage]
-  // [twiddles][mbarrier]
+  // serve as second exchange buffers.  Triplets: [input stage][output stage][twiddles][mbarrier]
   constexpr bool TRIP = TMAP && ZT::TRIP;
   constexpr int TWC = TRIP ? tw_cache_ns(N, E) : 0;  // second-stage twiddles kept in registers
   twv<T> twr[tw_cache_len(N, E)];
   C* stage = reinterpret_cast<C*>(zsmraw);
-  C* ostage = reinterpret_cast<C*>(zsmraw + ZT::stage_bytes + (TRIP ? ZT::xbuf_bytes : 0));
+  C* ostage = reinterpret_cast<C*>(zsmraw + ZT::stage_bytes);
   twv<T>* tw = reinterpret_cast<twv<T>*>(TMAP ? reinterpret_cast<unsigned char*>(ostage) + ZT::stage_bytes : zsmraw);
-  C* sm = TRIP ? reinterpret_cast<C*>(zsmraw + ZT::stage_bytes)
-               : reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(tw) + ZT::tw_bytes);
+  C* sm = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(tw) + ZT::tw_bytes);  // (not with triplets)
   uint64_t* full = reinterpret_cast<uint64_t*>(TRIP ? reinterpret_cast<unsigned char*>(tw) + ZT::tw_bytes
                                                     : reinterpret_cast<unsigned char*>(sm) + ZT::exch_bytes);
   for (int i = threadIdx.x; i < tw_len(N, E); i += blockDim.x) tw[i] = twg[i];
@@ -699,6 +702,13 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
         for (int m = 0; m < E; ++m) v[c][m] = stage[ZT::stage_index(c, t + P * m, x)];
       __syncthreads();  // every read of the stage is done (and the twiddles are in)
       pending = false;
+      if constexpr (TRIP) {
+        // the stage's upper half is free until the next tile: its copies start now
+        if (threadIdx.x == 0 && tile + gridDim.x < ntiles) {
+          z_tile_copy<T, N, E, TX, ZT::NB / 2, ZT::NB, true>(tmap, stage, full, tile + gridDim.x, ntx);
+          pending = true;
+        }
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < 6; ++c)
@@ -734,12 +744,13 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
     constexpr int LX = N * TX;  // complex values per unpadded exchange buffer
     if constexpr (TRIP) {
       static_assert(sizeof(CoefT) == 32, "coefficient entries of 32 bytes");
-      // three components at a time through the input stage's last two buffers' worth and the one
-      // after it (the coefficients fill the start of the stage)
-      C* fb = reinterpret_cast<C*>(zsmraw + ZT::stage_bytes - 2 * ZT::xbuf_bytes);
+      // three components at a time through the output stage, as the inverse transforms, once the
+      // previous tile's store has read it
+      if (threadIdx.x == 0) bulk_wait_read_all();
+      __syncthreads();
 #pragma unroll
       for (int c = 0; c < 6; c += 3)
-        zf_fwd<T, N, E, 3, false, TWC>(v + c, fb + x, SWZ, LX, t, tw, nullptr, twr);
+        zf_fwd<T, N, E, 3, true, TWC>(v + c, ostage + x, SWZ, LX, t, tw, ostage + 3 * LX + x, twr);
     } else if constexpr (TMAP && ZT::coef_bytes + ZT::exch_bytes <= ZT::stage_bytes) {
       // two components at a time: the second exchange buffer is the input stage past the coefficients
       C* xb2 = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(stage) + ZT::coef_bytes);
@@ -798,7 +809,14 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
         if constexpr (INV) add_densities<T>(part, col == 0 ? (T)1 : (T)2, kx, ky, kz, hh, ee, eps, mu);
       }
     }
-    if constexpr (TMAP) {
+    if constexpr (TRIP) {
+      // the coefficient reads of the stage's lower half are done: it takes the next tile's lower
+      // boxes (async proxy after generic)
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0 && tile + gridDim.x < ntiles)
+        z_tile_copy<T, N, E, TX, 0, ZT::NB / 2, false>(tmap, stage, full, tile + gridDim.x, ntx);
+    } else if constexpr (TMAP) {
       // the stage's coefficient reads are done: it takes the next tile (async proxy after generic)
       fence_proxy_async_smem();
       // the previous tile's store has read the output stage: it is the inverse transforms' second

@@ -20,12 +20,12 @@ template <typename T> constexpr int zf_TX(int n) {
 
 #define MX_ZF_LENS(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(6) X(12) X(24) X(48) X(96) X(192) X(384)
 
-// Tensor map of the spectrum as [6][nz][ny][2 Mx] scalars, box [6][ZC][1][2 TX].
+// Tensor map of the spectrum as [6][nz][ny][2 Mx] scalars, box [3][ZC][1][2 TX].
 template <typename T, int N, int E, int TX>
 static bool z_tensor_map(CUtensorMap* m, const void* data, const GridParams& g) {
   using ZT = ZTile<T, N, E, TX>;
   const cuuint64_t dim[4] = {(cuuint64_t)2 * g.mx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 6};
-  const cuuint32_t box[4] = {(cuuint32_t)(2 * TX), 1, (cuuint32_t)ZT::ZC, 6};
+  const cuuint32_t box[4] = {(cuuint32_t)(2 * TX), 1, (cuuint32_t)ZT::ZC, 3};
   return tensor_map(m, (int)sizeof(T), 4, data, dim, box);
 }
 
@@ -39,7 +39,7 @@ cudaError_t zf_n(cx<T>* data, const GridParams& g, const void* tab, double t, co
     constexpr int TX = zf_TX<T>(N), P = N / E;
     using ZT = ZTile<T, N, E, TX>;
     static_assert(plan_ok(N, E), "plan");
-    static_assert(ZT::stage_bytes % (128 * ZT::NZC) == 0, "tensor-copy boxes start on 128-byte boundaries");
+    static_assert(ZT::stage_bytes % (128 * ZT::NB) == 0, "tensor-copy boxes start on 128-byte boundaries");
     const CoefT* tb = reinterpret_cast<const CoefT*>(tab);
     cudaError_t err;
     // with the tensor-copy prefetch when the stage fits beside the exchange buffers
