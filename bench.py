@@ -725,6 +725,19 @@ def reference_arm(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def tile_stream_ceiling(torch, mx, n):
+    """GB/s that HBM delivers for the fused z pass's access pattern without its arithmetic: tensor-copy
+    tiles of 4 columns x n x 6 components of the n^3 spectrum (rows of 32 bytes at a stride of one z
+    plane), and of 8 and 16 columns (64- and 128-byte rows) for comparison (mx_tile_stream, best of 5)."""
+    m = n // 2
+    buf = torch.zeros(6 * n * n * m * 2, dtype=torch.float32, device="cuda")
+    try:
+        return {str(8 * c): mx.tile_stream(buf.data_ptr(), m, n, n, c) for c in (4, 8, 16)}
+    finally:
+        del buf
+        torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -800,6 +813,7 @@ def main():
                                    alu_peak=alu["fp64_fma_flops"] if p == mx.MX_FP64 else None)[1]
 
     e2e = e2e_run(torch, mx, grid, args.steps, stream) if not args.shape else None
+    rows = tile_stream_ceiling(torch, mx, grid) if not args.shape and grid <= 512 else None
     batched = None
     if not args.no_secondary:
         batched = batch_run(torch, mx, peak, min(args.steps, 100), args.warmup, stream)
@@ -851,7 +865,14 @@ def main():
             "frac": achieved / peak,
             "traffic": traffic_for(f"{dom}_fp32_{grid}") if not args.shape else None,
             "algorithmic_bytes_per_launch": bytes_per_launch,
+            # the same bytes moved in the fused pass's tiles with no arithmetic: the ceiling of its
+            # access pattern (rows of 32 bytes), measured in this run
+            "pattern_ceiling": None if rows is None or dom != "z_fused" else {
+                "gbs": rows["32"], "rows_bytes": 32, "frac": achieved / rows["32"],
+                "source": "mx_tile_stream: tensor-copy tiles of 4 columns x 512 z x 6 components, read and "
+                          "written back, no arithmetic"},
         },
+        "tile_stream_gbs_by_row_bytes": rows,
         "step_hbm_roofline_frac": forms["precision_fp32_literal"]["step_hbm_roofline_frac"],
         "roofline_per_pass": per_pass,
         "schedule": schedule,

@@ -397,6 +397,20 @@ mx_status mx_debug_wait_limit(mx_ctx* ctx, long long tries);
  */
 mx_status mx_fma_peak(int precision, double* flops_per_s);
 
+/* Measurement of what HBM delivers for the access pattern of the fused z pass
+ * (no counterpart in the paper): buf holds a spectrum [6][nz][ny][mx] of
+ * complex FP32 (device memory, 16-byte aligned, left unchanged: every tile is
+ * read into shared memory by tensor copy and written back in place), moved in
+ * tiles of `cols` columns x nz x (24 / cols) components by one persistent
+ * block per SM, the next tile's copy in flight while a tile is stored.  The
+ * rows of a tile are cols x 8 bytes (cols = 4: 32 bytes, the fused pass's
+ * tiles; 8: 64; 16: 128) at a stride of one z plane.  *gbs = bytes read and
+ * written per launch / the best of `reps` timed launches (after one warm-up).
+ * MX_E_INVAL for a null or misaligned buffer, cols other than 4, 8, 16, mx not
+ * a multiple of cols, nz outside 2..512 or reps < 1; MX_E_TIMEOUT if a copy
+ * wait gave up. */
+mx_status mx_tile_stream(void* buf, int mx, int ny, int nz, int cols, int reps, double* gbs);
+
 /*
  * DFT-as-GEMM evaluation (a measurement, not a step of the method; the
  * paper's cost model, Sec. 2.5, puts the time in the transforms): applies

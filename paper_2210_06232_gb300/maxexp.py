@@ -106,6 +106,7 @@ def _load():
         "mx_debug_fail_alloc": (I, [LL]),
         "mx_debug_wait_limit": (I, [P, LL]),
         "mx_fma_peak": (I, [I, C.POINTER(D)]),
+        "mx_tile_stream": (I, [V, I, I, I, I, I, C.POINTER(D)]),
         "mx_dft8_stage_eval": (I, [I, V, V, LL, I, C.POINTER(D)]),
         "mx_sync": (I, [P]),
         "mx_strerror": (C.c_char_p, [I]),
@@ -157,6 +158,7 @@ mx_profile_read = _lib.mx_profile_read
 mx_debug_fail_alloc = _lib.mx_debug_fail_alloc
 mx_debug_wait_limit = _lib.mx_debug_wait_limit
 mx_fma_peak = _lib.mx_fma_peak
+mx_tile_stream = _lib.mx_tile_stream
 mx_dft8_stage_eval = _lib.mx_dft8_stage_eval
 
 
@@ -164,6 +166,15 @@ def fma_peak(precision):
     """Measured FMA throughput (flop/s, an FMA counting two) of the FP64 or FP32 pipe."""
     v = C.c_double(0)
     check(mx_fma_peak(int(precision), C.byref(v)), "mx_fma_peak")
+    return v.value
+
+
+def tile_stream(buf_ptr, mx_, ny, nz, cols, reps=5):
+    """GB/s that HBM delivers for z-line tiles of `cols` columns (rows of 8 cols bytes) of a
+    [6][nz][ny][mx_] complex FP32 spectrum at device address buf_ptr (left unchanged)."""
+    v = C.c_double(0)
+    check(mx_tile_stream(C.c_void_p(int(buf_ptr)), int(mx_), int(ny), int(nz), int(cols), int(reps), C.byref(v)),
+          "mx_tile_stream")
     return v.value
 mx_sync = _lib.mx_sync
 mx_strerror = _lib.mx_strerror
