@@ -289,7 +289,8 @@ def form_entry(name, grid, precision, form, ms, steps, prof, peak, inv, world, a
         "unit": UNIT,
         "ms_per_step": step_ms,
         "dtype": "f64" if precision == 0 else "f32",
-        "form": "spectral-resident (absolute time)" if form == 1 else "literal (3D R2C -> update -> 3D C2R per step)",
+        "form": {0: "literal (3D R2C -> update -> 3D C2R per step)", 1: "spectral-resident (absolute time)",
+                 2: "xy-resident (state: x-y spectrum; z forward -> update -> z inverse per step)"}[form],
         "hbm_passes_per_step": passes,
         "step_hbm_roofline_frac": (min_bytes / (step_ms / 1e3) / 1e9) / peak,
         "energy_rel_drift": drift(inv),
@@ -805,6 +806,7 @@ def main():
         alu = {"fp64_fma_flops": mx.fma_peak(mx.MX_FP64), "fp32_fma_flops": mx.fma_peak(mx.MX_FP32)}
         plan = [("fp64_literal", mx.MX_FP64, mx.MX_FORM_LITERAL, min(args.steps, 10)),
                 ("spectral_resident_fp32", mx.MX_FP32, mx.MX_FORM_SPECTRAL, args.steps),
+                ("xy_resident_fp32", mx.MX_FP32, mx.MX_FORM_XY, args.steps),
                 ("spectral_resident_fp64", mx.MX_FP64, mx.MX_FORM_SPECTRAL, min(args.steps, 50))]
         for nm, p, f, k in plan:
             _, ms2, prof2, _, inv2 = run_form(torch, mx, grid, p, f, k, 3, stream, dist)

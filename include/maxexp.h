@@ -61,8 +61,18 @@ typedef enum { MX_FP64 = 0, MX_FP32 = 1 } mx_precision;
  *                     steps 1-4 with t_end = t_n, phase c|k|t_n taken in
  *                     FP64).  Physical fields are produced by mx_read_fields
  *                     (Alg. 2 step 5).
+ *  MX_FORM_XY       : the state is the spectrum of the fields in x and y (the
+ *                     first two transforms of Alg. 1, run by mx_load_fields)
+ *                     with z in physical space; every step runs the z
+ *                     transform, Alg. 2 steps 1-4 with t_end = h and the
+ *                     inverse z transform in one pass over HBM (the literal
+ *                     step without its x and y transforms, which cancel
+ *                     between steps).  mx_read_fields runs the inverse y and
+ *                     x transforms on a copy, so the state is unchanged.  nz
+ *                     must have a fused plan (2^a, 3*2^a in FP32; 2^a in
+ *                     FP64), otherwise MX_E_UNSUPPORTED_N.
  */
-typedef enum { MX_FORM_LITERAL = 0, MX_FORM_SPECTRAL = 1 } mx_form;
+typedef enum { MX_FORM_LITERAL = 0, MX_FORM_SPECTRAL = 1, MX_FORM_XY = 2 } mx_form;
 
 /*
  * Discrete invariants of Sec. 4 at one time level.  E3..E6, M1, M2 hold the
@@ -92,7 +102,7 @@ typedef struct {
  *  eps, mu    : permittivity and permeability, positive (eq. maxsys).
  *  precision  : MX_FP64 or MX_FP32 (arithmetic and storage of the fields;
  *               phases and invariant sums are FP64 in both).
- *  form       : MX_FORM_LITERAL or MX_FORM_SPECTRAL.
+ *  form       : MX_FORM_LITERAL, MX_FORM_SPECTRAL or MX_FORM_XY.
  *  stream     : a cudaStream_t to order all work on, or NULL for the
  *               legacy default stream.
  * On success *out owns all device memory of the solver (its size is

@@ -8,6 +8,7 @@ binding.  Build it with ``python paper_2210_06232_gb300/build.py``.
 from .maxexp import (  # noqa: F401
     MX_FORM_LITERAL,
     MX_FORM_SPECTRAL,
+    MX_FORM_XY,
     MX_FP32,
     MX_FP64,
     MaxexpError,

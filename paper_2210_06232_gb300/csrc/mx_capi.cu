@@ -216,7 +216,8 @@ bool commensurate(const double nu[3], const int mmax[3], double* s0, int qa[3], 
 
 int coef_kind(const mx_ctx* c) {
   // 0 Coef<T> table, 1 CoefHL table, 2 Coef<T> direct, 3 CoefHL direct
-  const bool hl = (c->prec == MX_FP32 && c->form == MX_FORM_LITERAL);
+  // the repeated-step forms keep the coefficients as double-single pairs in FP32
+  const bool hl = (c->prec == MX_FP32 && (c->form == MX_FORM_LITERAL || c->form == MX_FORM_XY));
   return (c->table ? 0 : 2) + (hl ? 1 : 0);
 }
 
@@ -418,11 +419,13 @@ mx_status tune_t(mx_ctx* c) {
   MX_CHECK(c, cudaStreamIsCapturing(c->stream, &cap));
   if (cap != cudaStreamCaptureStatusNone) return MX_OK;  // never time inside a capture
   // the passes below overwrite the work buffers: the spectral state at t_n is recomputed on demand
-  if (c->form == MX_FORM_LITERAL && c->loaded) return MX_OK;  // literal state lives in `phys`
+  // literal state lives in `phys`, xy-resident state in `spec`
+  if ((c->form == MX_FORM_LITERAL || c->form == MX_FORM_XY) && c->loaded) return MX_OK;
   cudaEvent_t e0, e1;
   MX_CHECK(c, cudaEventCreate(&e0));
   MX_CHECK(c, cudaEventCreate(&e1));
-  const bool fused = c->form == MX_FORM_LITERAL && mx::zfused_supported(c->nz, c->prec == MX_FP64);
+  const bool fused =
+      (c->form == MX_FORM_LITERAL || c->form == MX_FORM_XY) && mx::zfused_supported(c->nz, c->prec == MX_FP64);
   for (int pass = 0; pass < P_COUNT; ++pass) {
     if (pass == P_Z_FUSED && !fused) continue;
     {
@@ -489,8 +492,10 @@ mx_status load_t(mx_ctx* c, const void* E, const void* H, int on_device, bool wa
     e = (const T*)c->phys;
     h = (const T*)((const char*)c->phys + fb);
   }
-  void* target = c->form == MX_FORM_SPECTRAL ? c->spec0 : c->spec;
+  // the record of t = 0 comes from the full 3D spectrum (xy-resident form: in the work buffer)
+  void* target = c->form == MX_FORM_LITERAL ? c->spec : c->spec0;
   MX_CHECK(c, forward3<T>(c, e, h, target));
+  if (c->form == MX_FORM_XY) MX_CHECK(c, forward3<T>(c, e, h, c->spec, false));  // the state: x and y only
   c->rec_n = 0;
   c->rec_t.clear();
   c->rec_step.clear();
@@ -521,7 +526,7 @@ mx_status load_random_t(mx_ctx* c, unsigned long long seed, double sigma) {
     sum *= sw;
   }
   const double amp = (double)c->ns / sqrt(std::max(sum, 1e-300) * 4.0 / 3.0);
-  void* target = c->form == MX_FORM_SPECTRAL ? c->spec0 : c->spec;
+  void* target = c->form == MX_FORM_LITERAL ? c->spec : c->spec0;
   {
     ProfScope ps(c, MX_K_GEN);
     MX_CHECK(c, mx::launch_gen_divfree<T>((C2<T>*)target, c->nh, c->g, seed, sigma, amp, c->stream));
@@ -532,9 +537,12 @@ mx_status load_random_t(mx_ctx* c, unsigned long long seed, double sigma) {
   mx_status st = ensure_records(c, 1);
   if (st != MX_OK) return st;
   MX_CHECK(c, spectral_pass<T>(c, 0, target, nullptr, 0.0, next_record(c, 0.0, 0)));
-  if (c->form == MX_FORM_LITERAL) {
+  if (c->form != MX_FORM_SPECTRAL) {
     const size_t fb = (size_t)3 * c->ns * c->es;
-    MX_CHECK(c, inverse3<T>(c, c->spec, (T*)c->phys, (T*)((char*)c->phys + fb)));
+    T* e = (T*)c->phys;
+    T* h = (T*)((char*)c->phys + fb);
+    MX_CHECK(c, inverse3<T>(c, target, e, h));
+    if (c->form == MX_FORM_XY) MX_CHECK(c, forward3<T>(c, e, h, c->spec, false));  // the state: x and y only
   }
   c->t = 0.0;
   c->step = 0;
@@ -579,6 +587,14 @@ mx_status step_t(mx_ctx* c, double h, long long nsteps, int every) {
         MX_CHECK(c, spectral_pass<T>(c, inv ? 2 : 1, c->spec, c->spec, h, record));
         MX_CHECK(c, inverse3<T>(c, c->spec, e, hh));
       }
+    } else if (c->form == MX_FORM_XY) {
+      // one pass: z forward -> update -> z inverse (output scaled by 1/nz) on the x-y spectrum
+      MX_CHECK(c, ensure_table<T>(c, h));
+      ProfScope ps(c, MX_K_ZFUSED);
+      const int code = pass_schedule(c, P_Z_FUSED);
+      MX_CHECK(c, mx::launch_z_fused<T>(coef_kind(c), (C2<T>*)c->spec, c->g, c->tab, h,
+                                        (const mx::twv<T>*)c->twz + c->twz_zf, zfused_grid(c, sched_bps(code)),
+                                        sched_pipelined(code), c->partials, c->counter, record, c->stream));
     } else {
       MX_CHECK(c, spectral_pass<T>(c, inv ? 2 : 1, c->spec0, c->spec, tn, record));
       c->spec_valid = true;
@@ -596,6 +612,27 @@ mx_status read_t(mx_ctx* c, void* E, void* H, int on_device, bool wait = true) {
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     MX_CHECK(c, cudaMemcpyAsync(E, c->phys, fb, kind, c->stream));
     MX_CHECK(c, cudaMemcpyAsync(H, (char*)c->phys + fb, fb, kind, c->stream));
+  } else if (c->form == MX_FORM_XY) {
+    // the inverse y and x passes on a copy of the state
+    MX_CHECK(c, cudaMemcpyAsync(c->spec0, c->spec, (size_t)6 * c->nh * c->cs, cudaMemcpyDeviceToDevice, c->stream));
+    T* e = on_device ? (T*)E : (T*)c->phys;
+    T* h = on_device ? (T*)H : (T*)((char*)c->phys + fb);
+    {
+      ProfScope ps(c, MX_K_Y_FFT);
+      MX_CHECK(c, mx::launch_strided<T>(c->ny, +1, (C2<T>*)c->spec0, c->mx, 6LL * c->nz, (const mx::twv<T>*)c->twy,
+                                        pass_bps(c, P_Y_INV), c->stream, pass_pipe(c, P_Y_INV), pass_dbuf(c, P_Y_INV)));
+    }
+    {
+      const long long rows = (long long)c->ny * c->nz;
+      ProfScope ps(c, MX_K_X_C2R);
+      // the z transforms of every step carried their 1/nz: the x pass scales by 1/(nx ny)
+      MX_CHECK(c, mx::launch_x_c2r<T>(c->mx, (C2<T>*)c->spec0, e, h, 3 * rows, 6 * rows, (const mx::twv<T>*)c->twx,
+                                      1.0 / ((double)c->nx * c->ny), pass_bps(c, P_X_C2R), c->stream, pass_pipe(c, P_X_C2R)));
+    }
+    if (!on_device) {
+      MX_CHECK(c, cudaMemcpyAsync(E, c->phys, fb, cudaMemcpyDeviceToHost, c->stream));
+      MX_CHECK(c, cudaMemcpyAsync(H, (char*)c->phys + fb, fb, cudaMemcpyDeviceToHost, c->stream));
+    }
   } else {
     if (!c->spec_valid) MX_CHECK(c, spectral_pass<T>(c, 1, c->spec0, c->spec, c->t, nullptr));
     T* e = on_device ? (T*)E : (T*)c->phys;
@@ -616,7 +653,7 @@ size_t footprint(int nx, int ny, int nz, int prec, int form, int nq) {
   const size_t ns = (size_t)nx * ny * nz;
   size_t b = 6 * ns * es;                  // phys
   b += 6 * ns * es;                        // spec (nh complex == ns reals)
-  if (form == MX_FORM_SPECTRAL) b += 6 * ns * es;  // spec0
+  if (form != MX_FORM_LITERAL) b += 6 * ns * es;  // spec0 (xy-resident form: the work copy of reads)
   b += (size_t)nq * 32;                    // table
   b += (size_t)(nx + ny + 2 * nz) * 16;   // twiddles (16-byte entries)
   b += (size_t)152 * 4 * 16 * sizeof(double) + 64 * REC_STRIDE * sizeof(double) + 256;
@@ -650,7 +687,7 @@ const char* mx_strerror(mx_status s) {
 mx_status mx_footprint_bytes(int nx, int ny, int nz, int precision, int form, size_t* bytes) {
   if (!bytes || nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2) return MX_E_INVAL;
   if (precision != MX_FP64 && precision != MX_FP32) return MX_E_INVAL;
-  if (form != MX_FORM_LITERAL && form != MX_FORM_SPECTRAL) return MX_E_INVAL;
+  if (form != MX_FORM_LITERAL && form != MX_FORM_SPECTRAL && form != MX_FORM_XY) return MX_E_INVAL;
   // worst-case table size for a cubic-cell grid
   const long long nq = 1 + (long long)(nx / 2 - 1) * (nx / 2 - 1) + (long long)(ny / 2 - 1) * (ny / 2 - 1) +
                        (long long)(nz / 2 - 1) * (nz / 2 - 1);
@@ -668,9 +705,11 @@ mx_status mx_create(mx_ctx** out, int nx, int ny, int nz, const double lo[3], co
   for (int w = 0; w < 3; ++w)
     if (!isfinite(lo[w]) || !isfinite(hi[w]) || !(hi[w] > lo[w])) return MX_E_INVAL;
   if (precision != MX_FP64 && precision != MX_FP32) return MX_E_INVAL;
-  if (form != MX_FORM_LITERAL && form != MX_FORM_SPECTRAL) return MX_E_INVAL;
+  if (form != MX_FORM_LITERAL && form != MX_FORM_SPECTRAL && form != MX_FORM_XY) return MX_E_INVAL;
   if (!len_ok(nx / 2) || nx / 2 > 256 || !len_ok(ny) || !len_ok(nz)) return MX_E_UNSUPPORTED_N;
   if (6LL * nz > 65535) return MX_E_UNSUPPORTED_N;
+  // the xy-resident form steps with the fused z pass only
+  if (form == MX_FORM_XY && !mx::zfused_supported(nz, precision == MX_FP64)) return MX_E_UNSUPPORTED_N;
 
   mx_ctx* c = new mx_ctx();
   c->nx = nx; c->ny = ny; c->nz = nz; c->mx = nx / 2;
@@ -686,6 +725,10 @@ mx_status mx_create(mx_ctx** out, int nx, int ny, int nz, const double lo[3], co
   g.nx = nx; g.ny = ny; g.nz = nz; g.mx = c->mx;
   grid_info(nx, ny, nz, lo, hi, g.nu, mmax);
   mx::set_material(g, eps, mu);
+  if (form == MX_FORM_XY) {  // the fused pass's output is the state: its inverse z transform carries 1/nz
+    g.zscale = 1.0 / nz;
+    g.zscalef = (float)g.zscale;
+  }
   g.s0 = 0.0; g.qa[0] = g.qa[1] = g.qa[2] = 0;
   c->nq = 0;
   c->table = commensurate(g.nu, mmax, &g.s0, g.qa, &c->nq);
@@ -698,7 +741,7 @@ mx_status mx_create(mx_ctx** out, int nx, int ny, int nz, const double lo[3], co
   const size_t field_bytes = (size_t)6 * c->ns * c->es;
   if (mx::dev_alloc(&c->phys, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
   if (mx::dev_alloc(&c->spec, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
-  if (form == MX_FORM_SPECTRAL && mx::dev_alloc(&c->spec0, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
+  if (form != MX_FORM_LITERAL && mx::dev_alloc(&c->spec0, field_bytes) != cudaSuccess) return fail(MX_E_NOMEM);
   if (c->table && mx::dev_alloc(&c->tab, (size_t)c->nq * 32) != cudaSuccess) return fail(MX_E_NOMEM);
   // partial sums for up to 2 blocks per SM of any pass that reduces invariants
   c->pblocks = std::max(c->sblocks, 2 * mx::num_sms());

@@ -37,6 +37,11 @@ struct GridParams {
   // tries of the fused z pass's waits for its tiles (MBAR_TRIES unless a test lowers it to make
   // them give up; the wait for a copy still in flight when a block leaves keeps the full bound)
   unsigned wait_tries = 1u << 24;
+  // factor of the fused z pass's output (its inverse transforms carry no 1/nz): 1 where the
+  // inverse x pass applies the whole normalisation (literal form), 1/nz where the output stays
+  // the state between steps (xy-resident form)
+  double zscale = 1.0;
+  float zscalef = 1.0f;
 };
 // Material constants of a grid (host side; after nu is set).
 inline void set_material(GridParams& g, double eps, double mu) {
@@ -52,11 +57,13 @@ inline void set_material(GridParams& g, double eps, double mu) {
 // eps, mu and nu_w in the kernel's arithmetic type.
 template <typename T> struct GP;
 template <> struct GP<float> {
+  __device__ __forceinline__ static float zscale(const GridParams& g) { return g.zscalef; }
   __device__ __forceinline__ static float eps(const GridParams& g) { return g.epsf; }
   __device__ __forceinline__ static float mu(const GridParams& g) { return g.muf; }
   __device__ __forceinline__ static float nu(const GridParams& g, int w) { return g.nuf[w]; }
 };
 template <> struct GP<double> {
+  __device__ __forceinline__ static double zscale(const GridParams& g) { return g.zscale; }
   __device__ __forceinline__ static double eps(const GridParams& g) { return g.eps; }
   __device__ __forceinline__ static double mu(const GridParams& g) { return g.mu; }
   __device__ __forceinline__ static double nu(const GridParams& g, int w) { return g.nu[w]; }
@@ -859,6 +866,13 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
     } else {
 #pragma unroll
       for (int c = 0; c < 6; c += ZT::NL) zf_inv<T, N, E, ZT::NL>(v + c, sm + x, TX, LS, t, tw);
+    }
+    if (g.zscalef != 1.0f) {  // block-uniform; exact for nz a power of two
+      const T sc = GP<T>::zscale(g);
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[c][m] = C{v[c][m].x * sc, v[c][m].y * sc};
     }
     if constexpr (TMAP) {
       // through the output stage and the tensor-copy engine (it drops the columns past Mx)

@@ -18,7 +18,7 @@ LIB_PATH = os.environ.get("MAXEXP_LIB") or os.path.join(_PKG, "lib", "libmaxexp.
 
 MX_OK, MX_E_INVAL, MX_E_UNSUPPORTED_N, MX_E_NOMEM, MX_E_CUDA, MX_E_TIMEOUT, MX_E_STATE = range(7)
 MX_FP64, MX_FP32 = 0, 1
-MX_FORM_LITERAL, MX_FORM_SPECTRAL = 0, 1
+MX_FORM_LITERAL, MX_FORM_SPECTRAL, MX_FORM_XY = 0, 1, 2
 KERNEL_KINDS = ("x_r2c", "x_c2r", "y_fft", "z_fft", "spectral", "table", "gen", "z_fused")
 
 

@@ -57,6 +57,10 @@ def test_argument_validation_without_gpu():
         assert not h.value
     for nx, ny, nz in [(14, 8, 8), (8, 14, 8), (8, 8, 1024), (1026, 8, 8)]:
         assert mx.mx_create(C.byref(h), nx, ny, nz, lo, hi, 1.0, 1.0, 0, 0, None) == mx.MX_E_UNSUPPORTED_N
+    # the xy-resident form needs a fused z plan: 10 (5 * 2) has none; 6 has one in FP32 only
+    for nz, p in [(10, 1), (10, 0), (6, 0)]:
+        assert mx.mx_create(C.byref(h), 8, 8, nz, lo, hi, 1.0, 1.0, p, mx.MX_FORM_XY, None) == mx.MX_E_UNSUPPORTED_N
+        assert not h.value
     hi_bad = (C.c_double * 3)(1, 0, 1)
     assert mx.mx_create(C.byref(h), 8, 8, 8, lo, hi_bad, 1.0, 1.0, 0, 0, None) == mx.MX_E_INVAL
     assert mx.mx_create(None, 8, 8, 8, lo, hi, 1.0, 1.0, 0, 0, None) == mx.MX_E_INVAL
@@ -70,6 +74,9 @@ def test_footprint_is_host_only_and_scales():
     mx = _lib()
     b64 = mx.footprint_bytes((512, 512, 512), mx.MX_FP64, mx.MX_FORM_SPECTRAL)
     b32 = mx.footprint_bytes((512, 512, 512), mx.MX_FP32, mx.MX_FORM_SPECTRAL)
+    # the xy-resident form holds the same three field-sized buffers as the spectral one
+    assert mx.footprint_bytes((512, 512, 512), mx.MX_FP32, mx.MX_FORM_XY) == b32
+    assert mx.footprint_bytes((512, 512, 512), mx.MX_FP32, mx.MX_FORM_LITERAL) < b32
     assert b64 > 18 * 512 ** 3 * 8 * 0.99 and b32 < b64
     with pytest.raises(mx.MaxexpError):
         mx.footprint_bytes((7, 8, 8))
