@@ -104,3 +104,35 @@ def test_xy_form_is_the_literal_map(prec):
     assert max_field_rel_l2(xy[0], xy[1], lit[0], lit[1]) < (1e-12 if prec == "fp64" else 1e-5)
     for a, b in zip(lit[2], xy[2]):
         assert abs(a["E1"] - b["E1"]) <= (1e-13 if prec == "fp64" else 1e-6) * abs(a["E1"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_xy_form_random_load_and_autotune_match_the_spectral_form(prec):
+    # mx_load_random_divfree and mx_autotune in the xy-resident form: n steps of h equal the
+    # spectral-resident form's R(n h) applied to the same generated spectrum (group property)
+    import torch
+
+    mx = solver_mod()
+    g = synth.Grid((32, 16, 64), (0.0, 0.0, 0.0), (TWO_PI, TWO_PI, TWO_PI))
+    P = mx.MX_FP64 if prec == "fp64" else mx.MX_FP32
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    out = []
+    for F in (mx.MX_FORM_XY, mx.MX_FORM_SPECTRAL):
+        s = mx.Solver(g.n, g.lo, g.hi, 1.4, 0.9, P, F)
+        try:
+            s.autotune()
+            s.load_random(11, 6.0)
+            s.step(0.03, 20, 5)
+            E = torch.empty((3,) + g.shape, dtype=dt, device="cuda")
+            H = torch.empty_like(E)
+            s.read(E, H)
+            s.sync()
+            out.append((E.double().cpu().numpy(), H.double().cpu().numpy(), s.invariants()))
+        finally:
+            s.close()
+    (Ex, Hx, ix), (Es, Hs, is_) = out
+    assert max_field_rel_l2(Ex, Hx, Es, Hs) < (1e-12 if prec == "fp64" else 1e-5)
+    assert len(ix) == len(is_) == 5
+    for a, b in zip(ix, is_):
+        assert a["step"] == b["step"]
+        assert abs(a["E1"] - b["E1"]) <= (1e-12 if prec == "fp64" else 1e-6) * abs(b["E1"])
