@@ -232,6 +232,9 @@ mx_status mx_batch_create(mx_batch** out, const mx_instance_desc* inst, int n, i
  * stream per instance), captured once per (K, every, step phases) and
  * replayed; the records the graph writes are appended to each instance's
  * list after the launch.  Instances are bit-identical alone or in any batch.
+ * form = MX_FORM_XY: the same with xy-resident contexts (each step one fused
+ * z pass per instance); every instance's nz needs a fused plan, otherwise
+ * MX_E_UNSUPPORTED_N.
  * mx_batch_create is mx_batch_create_form with MX_FORM_SPECTRAL.
  */
 mx_status mx_batch_create_form(mx_batch** out, const mx_instance_desc* inst, int n, int precision, int form,

@@ -241,7 +241,7 @@ mx_status mx_batch_create_form(mx_batch** out, const mx_instance_desc* inst, int
   *out = nullptr;
   if (!inst || n < 1 || n > 4096) return MX_E_INVAL;
   if (precision != MX_FP64 && precision != MX_FP32) return MX_E_INVAL;
-  if (form != MX_FORM_SPECTRAL && form != MX_FORM_LITERAL) return MX_E_INVAL;
+  if (form != MX_FORM_SPECTRAL && form != MX_FORM_LITERAL && form != MX_FORM_XY) return MX_E_INVAL;
   mx_batch* b = new mx_batch();
   b->n = n;
   b->prec = precision;
@@ -259,12 +259,12 @@ mx_status mx_batch_create_form(mx_batch** out, const mx_instance_desc* inst, int
     mx_batch_destroy(b);
     return s;
   };
-  if (form == MX_FORM_LITERAL) {
+  if (form != MX_FORM_SPECTRAL) {  // literal or xy-resident: a graph of every instance's own passes
     for (int i = 0; i < n; ++i) {
       if (!isfinite(inst[i].h)) return bail(MX_E_INVAL);
       mx_ctx* c = nullptr;
       mx_status st = mx_create(&c, inst[i].nx, inst[i].ny, inst[i].nz, inst[i].lo, inst[i].hi, inst[i].eps, inst[i].mu,
-                               precision, MX_FORM_LITERAL, stream);
+                               precision, form, stream);
       if (st != MX_OK) return bail(st);
       b->ctx.push_back(c);
       b->h.push_back(inst[i].h);
@@ -372,7 +372,7 @@ mx_status mx_batch_step(mx_batch* b, long long nsteps, int invariants_every) {
   if (nsteps == 0) return MX_OK;
   for (int i = 0; i < b->n; ++i)
     if (!b->ctx[i]->loaded) return MX_E_STATE;
-  if (b->form == MX_FORM_LITERAL) {
+  if (b->form != MX_FORM_SPECTRAL) {
     const mx_status st = step_literal(b, nsteps, invariants_every);
     if (st != MX_OK && st != MX_E_INVAL && st != MX_E_STATE) b->err = st;
     return st;
@@ -441,7 +441,7 @@ mx_status mx_batch_sync(mx_batch* b) {
   if (!b) return MX_E_INVAL;
   if (b->err != MX_OK) return b->err;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(b, cudaErrorUnknown);
-  if (b->form == MX_FORM_LITERAL) {
+  if (b->form != MX_FORM_SPECTRAL) {
     for (int i = 0; i < b->n; ++i) {
       const mx_status st = mx_sync(b->ctx[i]);  // latched errors and timed-out waits of the instance
       if (st != MX_OK) {
@@ -462,8 +462,8 @@ mx_status mx_batch_sync(mx_batch* b) {
 
 mx_status mx_batch_launch_shape(mx_batch* b, int* blocks, int* threads) {
   if (!b || !blocks || !threads) return MX_E_INVAL;
-  *blocks = b->form == MX_FORM_LITERAL ? 0 : b->grid;
-  *threads = b->form == MX_FORM_LITERAL ? 0 : mx::BT_THREADS;
+  *blocks = b->form != MX_FORM_SPECTRAL ? 0 : b->grid;
+  *threads = b->form != MX_FORM_SPECTRAL ? 0 : mx::BT_THREADS;
   return MX_OK;
 }
 

@@ -351,7 +351,8 @@ class Batch:
 
     def __init__(self, instances, precision=MX_FP32, stream=None, form=MX_FORM_SPECTRAL):
         """instances: list of dicts with keys n=(nx,ny,nz), lo, hi, eps, mu, h; form MX_FORM_SPECTRAL
-        (one persistent launch per step call) or MX_FORM_LITERAL (graph of per-instance pass chains)."""
+        (one persistent launch per step call), MX_FORM_LITERAL or MX_FORM_XY (graph of per-instance pass
+        chains)."""
         arr = (mx_instance_desc * len(instances))()
         for i, d in enumerate(instances):
             arr[i].nx, arr[i].ny, arr[i].nz = (int(v) for v in d["n"])

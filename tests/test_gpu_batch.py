@@ -135,10 +135,10 @@ def test_batch_matches_oracle_per_field(prec):
     b.close()
 
 
-def _run_literal_batch(mx, specs, prec, inits, steps, every, calls=2):
+def _run_literal_batch(mx, specs, prec, inits, steps, every, calls=2, form=None):
     import torch
 
-    b = mx.Batch(specs, prec, form=mx.MX_FORM_LITERAL)
+    b = mx.Batch(specs, prec, form=mx.MX_FORM_LITERAL if form is None else form)
     npdt = np.float64 if prec == mx.MX_FP64 else np.float32
     for i, (E0, H0) in enumerate(inits):
         b.instance(i).load(E0.astype(npdt), H0.astype(npdt))
@@ -155,8 +155,9 @@ def _run_literal_batch(mx, specs, prec, inits, steps, every, calls=2):
     return out, used
 
 
+@pytest.mark.parametrize("form", ["literal", "xy"])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_literal_batch_alone_equals_in_mix_and_matches_oracle(prec):
+def test_literal_batch_alone_equals_in_mix_and_matches_oracle(prec, form):
     """Literal-form batch (every instance's x, y, fused z, y, x passes as parallel graph branches, with
     its shape's autotuned schedules): bit-identical alone and in the mix, each of the six fields
     against the oracle's literal stepping (Alg. 1 + Alg. 2 with t_end = h, repeated) within 1e-12
@@ -167,7 +168,13 @@ def test_literal_batch_alone_equals_in_mix_and_matches_oracle(prec):
     P = mx.MX_FP64 if prec == "fp64" else mx.MX_FP32
     npdt = np.float64 if prec == "fp64" else np.float32
     tol = 1e-12 if prec == "fp64" else 1e-5
-    specs = [SPECS[3], SPECS[4], dict(n=(16, 12, 32), eps=1.7, mu=0.6, h=0.043), dict(n=(20, 24, 80), eps=2.2, mu=1.4, h=0.03)]
+    F = mx.MX_FORM_LITERAL if form == "literal" else mx.MX_FORM_XY
+    if form == "literal":
+        specs = [SPECS[3], SPECS[4], dict(n=(16, 12, 32), eps=1.7, mu=0.6, h=0.043),
+                 dict(n=(20, 24, 80), eps=2.2, mu=1.4, h=0.03)]
+    else:  # the xy-resident form needs fused plans for nz (FP64: 2^a)
+        specs = [dict(n=(24, 20, 16), lo=(0, 0, 0), hi=(2.0, 3.0, 2.5), eps=2.0, mu=1.0, h=0.05), SPECS[4],
+                 dict(n=(16, 12, 32), eps=1.7, mu=0.6, h=0.043), dict(n=(20, 24, 64), eps=2.2, mu=1.4, h=0.03)]
     inits = []
     for i, sp in enumerate(specs):
         g = synth.Grid(sp["n"], sp.get("lo", (0, 0, 0)), sp.get("hi", (TWO_PI,) * 3))
@@ -175,10 +182,10 @@ def test_literal_batch_alone_equals_in_mix_and_matches_oracle(prec):
         inits.append((rng.standard_normal((3,) + g.shape).astype(npdt).astype(np.float64),
                       rng.standard_normal((3,) + g.shape).astype(npdt).astype(np.float64)))
     steps, every = 3, 1
-    mix, used = _run_literal_batch(mx, specs, P, inits, steps, every)
+    mix, used = _run_literal_batch(mx, specs, P, inits, steps, every, form=F)
     assert used == 1, f"graph capture refused: CUDA error {-used}"
     for i, sp in enumerate(specs):
-        alone, _ = _run_literal_batch(mx, [sp], P, [inits[i]], steps, every)
+        alone, _ = _run_literal_batch(mx, [sp], P, [inits[i]], steps, every, form=F)
         np.testing.assert_array_equal(mix[i][0], alone[0][0])
         np.testing.assert_array_equal(mix[i][1], alone[0][1])
         assert len(mix[i][2]) == len(alone[0][2]) == 1 + 2 * steps
