@@ -301,7 +301,7 @@ mx_status mx_batch_create_form(mx_batch** out, const mx_instance_desc* inst, int
   b->total_q = (unsigned)q;
   if (mx::host_alloc_pinned((void**)&b->h_inst, sizeof(mx::BInst) * n) != cudaSuccess) return bail(MX_E_NOMEM);
   if (mx::dev_alloc((void**)&b->d_inst, sizeof(mx::BInst) * n) != cudaSuccess) return bail(MX_E_NOMEM);
-  if (mx::dev_alloc((void**)&b->cpart, (size_t)b->total_chunks * mx::BT_CWARPS * mx::NSUM * sizeof(double)) != cudaSuccess)
+  if (mx::dev_alloc((void**)&b->cpart, (size_t)b->total_chunks * mx::BT_CWARPS * 16 * sizeof(double)) != cudaSuccess)
     return bail(MX_E_NOMEM);
   if (mx::dev_alloc((void**)&b->bar, 64) != cudaSuccess) return bail(MX_E_NOMEM);
   if (cudaMemset(b->bar, 0, 64) != cudaSuccess) return bail(MX_E_CUDA);
@@ -321,7 +321,7 @@ mx_status mx_batch_create_form(mx_batch** out, const mx_instance_desc* inst, int
     d.nchunks = (unsigned)((c->nh + ch - 1) / ch);
     d.q0 = q0;
     d.seg0 = s0;
-    d.nseg = (d.nchunks * mx::BT_CWARPS + mx::BT_SEG - 1) / mx::BT_SEG;
+    d.nseg = (d.nchunks + mx::BT_SEGC - 1) / mx::BT_SEGC;
     d.h = b->h[i];
     c0 += d.nchunks;
     q0 += (unsigned)d.nq;

@@ -10,7 +10,8 @@
 //            chunks (CH points x 6 components) spanning all instances, consumed
 //            by the same warp-specialised bulk-copy pipeline as the single
 //            pass; each warp writes its invariant partial sums of the chunk
-//            to `cpart[chunk][warp]` when step n is recorded;
+//            (in the instance's precision) to `cpart[chunk][warp]` when step
+//            n is recorded;
 //   barrier.
 // Chunk contents and warp partitions depend only on the instance's own chunk
 // index, and records are summed per instance over its own chunks in order,
@@ -32,7 +33,7 @@ struct BInst {
   unsigned chunk0;   // first global chunk of this instance
   unsigned nchunks;
   unsigned q0;       // first index of this instance in the concatenated table range
-  unsigned seg0;     // first invariant segment (BT_SEG chunk-warp partials) of this instance
+  unsigned seg0;     // first invariant segment (BT_SEGC chunks) of this instance
   unsigned nseg;
   long long n0;      // step count before this launch
   double t0, h;      // time before this launch, step size: t_n = t0 + (n - n0) h
@@ -47,8 +48,8 @@ struct BatchArgs {
   unsigned total_q;
   int nsteps;
   unsigned total_segs;
-  double* cpart;   // [total_chunks][BT_CWARPS][NSUM]: per-warp partial sums of a chunk
-  double* segpart; // [2][total_segs][NSUM]: sums of BT_SEG consecutive chunk-warp partials
+  void* cpart;     // [total_chunks][BT_CWARPS][16] of T: per-warp partial sums of a chunk (value 15: 0)
+  double* segpart; // [2][total_segs][NSUM]: sums of BT_SEGC consecutive chunks
   unsigned* bar;  // [0] arrivals, [1] generation, [2] error flag
 };
 
@@ -63,7 +64,7 @@ constexpr int BT_NST = 4;
 constexpr int BT_CONSUMERS = 224;  // seven consumer warps + the producer: two blocks of eight warps per SM
 constexpr int BT_THREADS = BT_CONSUMERS + 32;
 constexpr int BT_CWARPS = BT_CONSUMERS / 32;
-constexpr int BT_SEG = 256;  // chunk-warp partials per invariant segment
+constexpr int BT_SEGC = 32;  // chunks per invariant segment (one lane each)
 template <typename T> __host__ __device__ constexpr int bt_ch() { return BT_CONSUMERS * BTraits<T>::PPT; }
 template <typename T> __host__ __device__ constexpr size_t bt_smem_bytes() {
   return (size_t)BT_NST * 6 * bt_ch<T>() * sizeof(cx<T>) + 16 * BT_NST + 32 * NSUM * sizeof(double);
@@ -148,42 +149,50 @@ __device__ __forceinline__ int find_inst_s(const BatchArgs& a, const unsigned* s
 }
 __device__ __forceinline__ long long rec_slot(const BInst& b, long long N) { return N / b.every - b.n0 / b.every - 1; }
 
-// Invariant records, a two-level fixed tree: segment j of an instance is the
-// sum of its chunk-warp partials [j*BT_SEG, (j+1)*BT_SEG) (one warp per
-// segment, lane-strided then a fixed shuffle tree); the record is the sum of
-// the instance's segments (one warp per instance).  Both levels depend only
-// on instance-local indices.
-__device__ __forceinline__ void warp_sum15(double* v) {
-#pragma unroll
-  for (int k = 0; k < NSUM; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-}
-
+// Invariant records, a fixed tree in three levels.  A chunk's sum is its
+// warps' partials added in warp order in the instance's precision (T; the
+// partials are sums of T densities already); segment j of an instance is the
+// FP64 sum of the chunk sums of its chunks [j*BT_SEGC, (j+1)*BT_SEGC), one lane
+// per chunk and a transposed warp tree; the record is the sum of the
+// instance's segments (one warp per instance).  Every level depends only on
+// instance-local indices.  On a part with a narrow FP64 pipe the transposed
+// trees (16 FP64 additions per lane where a butterfly per sum takes 75) and
+// the chunk-level sums in T keep phase A short.
+template <typename T>
 __device__ void batch_segments(const BatchArgs& a, long long step_local, double* seg) {
   const int lane = threadIdx.x & 31;
   const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const T* cp = reinterpret_cast<const T*>(a.cpart);
   for (unsigned sgi = gw; sgi < a.total_segs; sgi += nw) {
     const int ii = find_inst_seg(a.inst, a.ninst, sgi);
     const BInst& b = a.inst[ii];
     if (!recorded(b, b.n0 + step_local)) continue;  // uniform within the warp
-    const unsigned j = sgi - b.seg0;
-    const unsigned p0 = j * BT_SEG, p1 = min(p0 + BT_SEG, b.nchunks * BT_CWARPS);
-    double v[NSUM];
+    const unsigned c = (sgi - b.seg0) * BT_SEGC + lane;  // this lane's chunk of the instance
+    double v[16];
+    if (c < b.nchunks) {
+      const T* row = cp + (size_t)(b.chunk0 + c) * BT_CWARPS * 16;
+      // rows of 16 values, 64 (float) or 128 (double) bytes: 16-byte loads
+      using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+      constexpr int PER = (int)(sizeof(V) / sizeof(T));
+      T s[16];
 #pragma unroll
-    for (int k = 0; k < NSUM; ++k) v[k] = 0.0;
-    for (unsigned pr = p0 + lane; pr < p1; pr += 32) {
-      const double* p = a.cpart + ((size_t)b.chunk0 * BT_CWARPS + pr) * NSUM;
+      for (int w = 0; w < BT_CWARPS; ++w)
 #pragma unroll
-      for (int k = 0; k < NSUM; ++k) v[k] += __ldcg(p + k);
+        for (int q = 0; q < 16 / PER; ++q) {
+          const V x = __ldcg(reinterpret_cast<const V*>(row + w * 16) + q);
+          const T* e = reinterpret_cast<const T*>(&x);
+#pragma unroll
+          for (int u = 0; u < PER; ++u) s[q * PER + u] = w == 0 ? e[u] : s[q * PER + u] + e[u];
+        }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = (double)s[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = 0.0;
     }
-    warp_sum15(v);
-    if (lane < NSUM) {
-      double out = 0.0;
-#pragma unroll
-      for (int k = 0; k < NSUM; ++k) out = (lane == k) ? v[k] : out;
-      seg[(size_t)sgi * NSUM + lane] = out;
-    }
+    const double tot = warp_transpose_sum16<double>(v, lane);
+    const int idx = transpose_index(lane);
+    if (!(lane & 1) && idx < NSUM) seg[(size_t)sgi * NSUM + idx] = tot;
   }
 }
 
@@ -194,21 +203,17 @@ __device__ void batch_final(const BatchArgs& a, long long step_local, const doub
     const BInst& b = a.inst[ii];
     const long long N = b.n0 + step_local;
     if (!recorded(b, N)) continue;
-    double v[NSUM];
+    double v[16];
 #pragma unroll
-    for (int k = 0; k < NSUM; ++k) v[k] = 0.0;
+    for (int k = 0; k < 16; ++k) v[k] = 0.0;
     for (unsigned j = lane; j < b.nseg; j += 32) {
       const double* p = seg + (size_t)(b.seg0 + j) * NSUM;
 #pragma unroll
       for (int k = 0; k < NSUM; ++k) v[k] += __ldcg(p + k);
     }
-    warp_sum15(v);
-    if (lane < NSUM) {
-      double out = 0.0;
-#pragma unroll
-      for (int k = 0; k < NSUM; ++k) out = (lane == k) ? v[k] : out;
-      b.rec[(size_t)rec_slot(b, N) * 16 + lane] = out;
-    }
+    const double tot = warp_transpose_sum16<double>(v, lane);
+    const int idx = transpose_index(lane);
+    if (!(lane & 1) && idx < NSUM) b.rec[(size_t)rec_slot(b, N) * 16 + idx] = tot;
   }
 }
 
@@ -251,7 +256,7 @@ __global__ void __maxnreg__(112) k_batch_steps(BatchArgs a) {
               coef_direct<T, Coef<T>>(b.g.s0 * (double)qi, b.t0 + (double)n * b.h, b.g);
       }
     }
-    if (n >= 2 && n - 1 <= a.nsteps) batch_segments(a, n - 1, a.segpart + (size_t)((n - 1) & 1) * a.total_segs * NSUM);
+    if (n >= 2 && n - 1 <= a.nsteps) batch_segments<T>(a, n - 1, a.segpart + (size_t)((n - 1) & 1) * a.total_segs * NSUM);
     if (n >= 3) batch_final(a, n - 2, a.segpart + (size_t)((n - 2) & 1) * a.total_segs * NSUM);
     if (n == a.nsteps + 2) break;
     if (!grid_barrier(a.bar)) return;
@@ -392,7 +397,7 @@ __global__ void __maxnreg__(112) k_batch_steps(BatchArgs a) {
           v16[15] = (T)0;
           const T tot = warp_transpose_sum16<T>(v16, lane);
           const int idx = transpose_index(lane);
-          if (!(lane & 1) && idx < NSUM) a.cpart[((size_t)gc * BT_CWARPS + warp) * NSUM + idx] = (double)tot;
+          if (!(lane & 1)) reinterpret_cast<T*>(a.cpart)[((size_t)gc * BT_CWARPS + warp) * 16 + idx] = tot;
         }
       }
     }

@@ -299,13 +299,60 @@ __device__ __forceinline__ int transpose_index(int lane) {
   return ((lane & 16) ? 8 : 0) + ((lane & 8) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
 }
 
-// Block-wide FP64 reduction of NSUM values, then a deterministic grid
-// reduction by the last block to finish: partials[block][NSUM] -> record.
-// The counter must be zero on entry; the last block resets it.
+// Grid reduction of NSUM FP64 sums.  Every block hands in its totals as rows, one per warp
+// (rows[w][k], w < nrows), summed in warp order; the last block to finish sums the blocks'
+// partials in a fixed order and writes the record.  The counter must be zero on entry; the last
+// block resets it.  The order is that of a warp-wide tree over 32 consecutive "lanes" j (lane j
+// holding blocks j, j + blockDim.x, ...), then the groups of 32 in order, each tree summed by one
+// thread per (sum, group): on a part whose FP64 pipe is narrow, that is a few warp instructions
+// where a shuffle tree in every warp costs hundreds.  `grp` (shared, 32 rows; it may be `rows`)
+// holds the groups' sums in the last block.
+__device__ __forceinline__ void rows_finish(const double (*rows)[NSUM], int nrows, double (*grp)[NSUM],
+                                            double* __restrict__ partials,
+                                            unsigned* __restrict__ counter, double* __restrict__ record) {
+  __shared__ bool last;
+  const int nblocks = gridDim.x * gridDim.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (threadIdx.x < NSUM) {
+    double v = 0.0;
+    for (int w = 0; w < nrows; ++w) v += rows[w][threadIdx.x];
+    partials[(size_t)bid * NSUM + threadIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(nblocks - 1));
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int ngrp = (int)((blockDim.x + 31) >> 5);
+  const int q = threadIdx.x, w = q / NSUM, k = q - w * NSUM;
+  if (w < ngrp) {
+    double s[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      s[l] = 0.0;
+      for (int b = 32 * w + l; b < nblocks; b += blockDim.x) s[l] += __ldcg(partials + (size_t)b * NSUM + k);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int l = 0; l < o; ++l) s[l] += s[l + o];
+    grp[w][k] = s[0];
+  }
+  __syncthreads();
+  if (threadIdx.x < NSUM) {
+    double v = 0.0;
+    for (int g = 0; g < ngrp; ++g) v += grp[g][threadIdx.x];
+    record[threadIdx.x] = v;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// Block-wide FP64 reduction of NSUM values held by every thread (a warp tree, then the warps in
+// order), then the grid reduction of rows_finish.
 __device__ __forceinline__ void reduce_and_finish(double* acc, double* __restrict__ partials, unsigned* __restrict__ counter,
                                                   double* __restrict__ record) {
   __shared__ double red[32][NSUM];
-  __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int i = 0; i < NSUM; ++i) {
@@ -315,43 +362,7 @@ __device__ __forceinline__ void reduce_and_finish(double* acc, double* __restric
     if (lane == 0) red[warp][i] = v;
   }
   __syncthreads();
-  const int nblocks = gridDim.x * gridDim.y;
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  if (threadIdx.x < NSUM) {
-    double v = 0.0;
-    for (int w = 0; w < nwarps; ++w) v += red[w][threadIdx.x];
-    partials[(size_t)bid * NSUM + threadIdx.x] = v;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(nblocks - 1));
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  // fixed order: thread j sums blocks j, j + blockDim.x, ... then a fixed tree
-  double loc[NSUM];
-#pragma unroll
-  for (int i = 0; i < NSUM; ++i) loc[i] = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    const double* p = partials + (size_t)b * NSUM;
-#pragma unroll
-    for (int i = 0; i < NSUM; ++i) loc[i] += __ldcg(p + i);
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < NSUM; ++i) {
-    double v = loc[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][i] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < NSUM) {
-    double v = 0.0;
-    for (int w = 0; w < nwarps; ++w) v += red[w][threadIdx.x];
-    record[threadIdx.x] = v;
-  }
-  if (threadIdx.x == 0) *counter = 0u;
+  rows_finish(red, nwarps, red, partials, counter, record);
 }
 
 // ----------------------------------------------------------------- x passes
@@ -900,10 +911,11 @@ __device__ __forceinline__ void z_fused_body(cx<T>* __restrict__ data, const Gri
     if (threadIdx.x == 0) bulk_wait_all();  // the last stores have completed
   }
   if constexpr (INV) {
-    double acc[NSUM];
-#pragma unroll
-    for (int k = 0; k < NSUM; ++k) acc[k] = lane == 0 ? (double)zhi[warp][k] - (double)zlo[warp][k] : 0.0;
-    reduce_and_finish(acc, partials, counter, record);
+    // each warp's row of totals: lane k takes sum k (hi + (-lo)) to FP64
+    __shared__ double rows[32][NSUM];
+    if (lane < NSUM) rows[warp][lane] = (double)zhi[warp][lane] - (double)zlo[warp][lane];
+    __syncthreads();
+    rows_finish(rows, (int)((blockDim.x + 31) >> 5), rows, partials, counter, record);
   }
 }
 

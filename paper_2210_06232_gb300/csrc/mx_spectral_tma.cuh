@@ -189,10 +189,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 2)
   }
   if constexpr (INV) {
     __syncthreads();
-    double acc[NSUM];
-#pragma unroll
-    for (int k = 0; k < NSUM; ++k) acc[k] = (lane == 0 && warp < TMA_CWARPS) ? wsum[warp * NSUM + k] : 0.0;
-    reduce_and_finish(acc, partials, counter, record);
+    __shared__ double grp[32][NSUM];
+    rows_finish(reinterpret_cast<const double(*)[NSUM]>(wsum), TMA_CWARPS, grp, partials, counter, record);
   }
 }
 
