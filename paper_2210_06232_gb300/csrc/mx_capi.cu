@@ -72,8 +72,9 @@ mx_status cuda_fail(mx_ctx* c, cudaError_t e) {
     }                                                          \
   } while (0)
 
-// exp(-2 pi i j / n) for j < n in long double (at least 64-bit significands: the FP64 tables keep
-// hi + lo pairs), reduced to the first quadrant exactly when 4 | n.
+// exp(-2 pi i j / n) for j < n in long double (at least 64-bit significands: the FP32 tables keep
+// hi + lo pairs, the lifting constants are taken from the angle), reduced to the first quadrant
+// exactly when 4 | n.
 using ldvec = std::vector<long double>;
 void twiddles(int n, ldvec& re, ldvec& im) {
   const long double PI = 3.141592653589793238462643383279502884L;
@@ -146,8 +147,8 @@ void axis_twiddles(int axis, int n, bool fp64, ldvec& re, ldvec& im, int* zf_off
   }
 }
 
-// Entries hi + lo in the arithmetic type: FP64 dd2 (hi.x, hi.y, lo.x, lo.y), FP32 float4 the same,
-// except the FP32 fused z pass's lifting constants.
+// FP64 entries: lifting constants dd2 (p, u, sign, 0) of every twiddle.  FP32 entries: float4
+// hi + lo pairs, except the fused z pass's lifting constants (p, u, sign, 0).
 cudaError_t upload_twiddles(mx_ctx* c, int axis, int n, void** dst) {
   ldvec re, im;
   int zf_off = 0;
@@ -159,10 +160,15 @@ cudaError_t upload_twiddles(mx_ctx* c, int axis, int n, void** dst) {
   if (c->prec == MX_FP64) {
     cudaError_t e = mx::dev_alloc(dst, (size_t)n * sizeof(mx::dd2));
     if (e != cudaSuccess) return e;
+    // lifting constants (p, u, sign, 0) of the rotation by the twiddle's angle (mx_fft.cuh, twmul)
     std::vector<mx::dd2> h(n);
     for (int j = 0; j < n; ++j) {
-      const double rh = (double)re[j], ih = (double)im[j];
-      h[j] = mx::dd2{rh, ih, (double)(re[j] - (long double)rh), (double)(im[j] - (long double)ih)};
+      const long double PI = 3.141592653589793238462643383279502884L;
+      long double a = atan2l(im[j], re[j]);
+      double sg = 1.0;
+      if (a > PI / 2) a -= PI, sg = -1.0;
+      else if (a < -PI / 2) a += PI, sg = -1.0;
+      h[j] = mx::dd2{(double)(-tanl(0.5L * a)), (double)sinl(a), sg, 0.0};
     }
     return cudaMemcpy(*dst, h.data(), n * sizeof(mx::dd2), cudaMemcpyHostToDevice);
   }

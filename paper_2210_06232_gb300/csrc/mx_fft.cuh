@@ -24,23 +24,34 @@ template <> struct vec2<float> { using type = float2; };
 template <> struct vec2<double> { using type = double2; };
 template <typename T> using cx = typename vec2<T>::type;
 
-// Twiddle storage: the value as a pair hi + lo in the arithmetic type (FP32:
-// float4 hi.x, hi.y, lo.x, lo.y; FP64: the same in doubles).  Every FFT
-// constant is applied as hi + lo: a rounded constant would scale each
-// frequency by the same wrong factor on every transform, and in a repeated
-// forward/inverse loop that bias grows linearly with the step count.
-struct __align__(16) dd2 { double x, y, z, w; };  // hi.x, hi.y, lo.x, lo.y
+// Twiddle storage.  FP32: the value as a pair hi + lo (float4 hi.x, hi.y, lo.x,
+// lo.y); FP64: the lifting constants of the rotation (dd2 p, u, sign, 0; twmul
+// below).  A rounded cos/sin constant would scale each frequency by the same
+// wrong factor on every transform, and in a repeated forward/inverse loop that
+// bias grows linearly with the step count; neither form has that bias.
+struct __align__(16) dd2 { double x, y, z, w; };
 template <typename T> struct tw_t;
 template <> struct tw_t<float> { using type = float4; };
 template <> struct tw_t<double> { using type = dd2; };
 template <typename T> using twv = typename tw_t<T>::type;
 
-// a * w (forward, DIR < 0) or a * conj(w) (inverse)
+// a * w (forward, DIR < 0) or a * conj(w) (inverse).
+// FP64 twiddles are lifted rotations: entry (p, u, sign, 0) rotates by the twiddle's angle a as
+// three shears x += p y, y += u x, x += p y (p = -tan(a'/2), u = sin a'), where a' = a when
+// |a| <= pi/2 and a -+ pi otherwise (sign = -1: the input is negated first, by its sign bits, off
+// the FP64 pipe).  The inverse rotation takes -p, -u.  A product of shears has determinant 1 for
+// whatever rounded p and u, so the rounding of the constants scales no frequency on average (a
+// rounded cos/sin pair scales every value that passes through it by |w|^2 on every transform,
+// which a repeated step accumulates), at 3 FP64 operations where a double-double pair takes 8.
 template <int DIR> __device__ __forceinline__ double2 twmul(double2 a, dd2 w) {
-  const double hy = DIR < 0 ? w.y : -w.y, ly = DIR < 0 ? w.w : -w.w;
-  const double re = fma(a.x, w.x, fma(-a.y, hy, a.x * w.z - a.y * ly));
-  const double im = fma(a.x, hy, fma(a.y, w.x, a.x * ly + a.y * w.z));
-  return double2{re, im};
+  const double p = DIR < 0 ? w.x : -w.x, u = DIR < 0 ? w.y : -w.y;
+  const int sb = __double2hiint(w.z) & (int)0x80000000;
+  double x = __hiloint2double(__double2hiint(a.x) ^ sb, __double2loint(a.x));
+  double y = __hiloint2double(__double2hiint(a.y) ^ sb, __double2loint(a.y));
+  x = fma(p, y, x);
+  y = fma(u, x, y);
+  x = fma(p, y, x);
+  return double2{x, y};
 }
 template <int DIR> __device__ __forceinline__ float2 twmul(float2 a, float4 w) {
   const float hy = DIR < 0 ? w.y : -w.y, ly = DIR < 0 ? w.w : -w.w;
@@ -118,6 +129,40 @@ template <int DIR, int S, typename C> __device__ __forceinline__ void bfly8(C* v
     v[k * S] = cadd(e[k], o[k]);
     v[(k + 4) * S] = csub(e[k], o[k]);
   }
+}
+
+// FP64: the products by exp(DIR i pi/4) and exp(DIR 3 i pi/4) = -exp(-DIR i pi/4) as lifted
+// rotations (three shears, p = -tan(a/2), u = sin a; twmul): 3 FP64 operations where 1/sqrt(2)
+// as a double-double pair takes 6, and determinant 1 whatever the rounding of p and u.
+template <int DIR, int S> __device__ __forceinline__ void bfly8(double2* v) {
+  constexpr double TP8 = 0.41421356237309503;   // tan(pi/8) = sqrt(2) - 1
+  constexpr double S4 = 0.70710678118654757;    // sin(pi/4)
+  double2 e[4] = {v[0], v[2 * S], v[4 * S], v[6 * S]};
+  double2 o[4] = {v[S], v[3 * S], v[5 * S], v[7 * S]};
+  bfly4<DIR, 1>(e);
+  bfly4<DIR, 1>(o);
+  // rotation by a = DIR pi/4 (p = -DIR tan(pi/8), u = DIR sin(pi/4)) of o[1]; by -a of o[3],
+  // whose product is then subtracted where o[3] is added (the factor -1 of 3 pi/4 = pi - pi/4)
+  const double p = DIR < 0 ? TP8 : -TP8, u = DIR < 0 ? -S4 : S4;
+  double x = o[1].x, y = o[1].y;
+  x = fma(p, y, x);
+  y = fma(u, x, y);
+  x = fma(p, y, x);
+  o[1] = double2{x, y};
+  o[2] = rot<DIR>(o[2]);
+  x = o[3].x, y = o[3].y;
+  x = fma(-p, y, x);
+  y = fma(-u, x, y);
+  x = fma(-p, y, x);
+  o[3] = double2{x, y};
+  v[0] = cadd(e[0], o[0]);
+  v[4 * S] = csub(e[0], o[0]);
+  v[S] = cadd(e[1], o[1]);
+  v[5 * S] = csub(e[1], o[1]);
+  v[2 * S] = cadd(e[2], o[2]);
+  v[6 * S] = csub(e[2], o[2]);
+  v[3 * S] = csub(e[3], o[3]);
+  v[7 * S] = cadd(e[3], o[3]);
 }
 
 template <int DIR, int S, typename C> __device__ __forceinline__ void bfly3(C* v) {
