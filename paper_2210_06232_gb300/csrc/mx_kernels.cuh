@@ -327,12 +327,16 @@ __device__ __forceinline__ void rows_finish(const double (*rows)[NSUM], int nrow
   const int ngrp = (int)((blockDim.x + 31) >> 5);
   const int q = threadIdx.x, w = q / NSUM, k = q - w * NSUM;
   if (w < ngrp) {
+    // the first block of every lane in 32 independent loads issued together (a loop per lane would
+    // wait for each L2 round trip in turn), then the blocks past blockDim.x, added in the same order
     double s[32];
+    const int b0 = 32 * w;
 #pragma unroll
-    for (int l = 0; l < 32; ++l) {
-      s[l] = 0.0;
-      for (int b = 32 * w + l; b < nblocks; b += blockDim.x) s[l] += __ldcg(partials + (size_t)b * NSUM + k);
-    }
+    for (int l = 0; l < 32; ++l) s[l] = b0 + l < nblocks ? __ldcg(partials + (size_t)(b0 + l) * NSUM + k) : 0.0;
+    for (int r = (int)blockDim.x; b0 + r < nblocks; r += (int)blockDim.x)
+#pragma unroll
+      for (int l = 0; l < 32; ++l)
+        if (b0 + r + l < nblocks) s[l] += __ldcg(partials + (size_t)(b0 + r + l) * NSUM + k);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
