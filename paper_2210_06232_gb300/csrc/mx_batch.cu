@@ -33,6 +33,7 @@ struct mx_batch {
   mx::BInst* d_inst = nullptr;
   double* cpart = nullptr;
   double* segpart = nullptr;
+  mx::QK* qk = nullptr;  // FP32: per table entry, (0.5 c)|k|, |k|, |k|^2
   unsigned* bar = nullptr;
   unsigned total_chunks = 0, total_q = 0, total_segs = 0;
   int grid = 0;
@@ -65,6 +66,7 @@ cudaError_t launch_batch(mx_batch* b, int nsteps) {
   a.total_segs = b->total_segs;
   a.cpart = b->cpart;
   a.segpart = b->segpart;
+  a.qk = b->qk;
   a.bar = b->bar;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->grid);
@@ -330,6 +332,20 @@ mx_status mx_batch_create_form(mx_batch** out, const mx_instance_desc* inst, int
   b->total_segs = s0;
   if (mx::dev_alloc((void**)&b->segpart, (size_t)2 * b->total_segs * mx::NSUM * sizeof(double)) != cudaSuccess)
     return bail(MX_E_NOMEM);
+  if (precision == MX_FP32 && b->total_q > 0) {
+    // what phase A's coefficients take from |k| alone, as coef_direct forms it
+    std::vector<mx::QK> qk(b->total_q);
+    for (int i = 0; i < n; ++i) {
+      const mx::BInst& d = b->h_inst[i];
+      for (int qi = 0; qi < d.nq; ++qi) {
+        const double k2 = d.g.s0 * (double)qi, kabs = std::sqrt(k2);
+        qk[d.q0 + qi] = mx::QK{0.5 * d.g.c * kabs, (float)kabs, (float)k2};
+      }
+    }
+    if (mx::dev_alloc((void**)&b->qk, qk.size() * sizeof(mx::QK)) != cudaSuccess) return bail(MX_E_NOMEM);
+    if (cudaMemcpy(b->qk, qk.data(), qk.size() * sizeof(mx::QK), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(MX_E_CUDA);
+  }
   // co-resident grid for the cooperative launch
   const void* kern = precision == MX_FP64 ? batch_kernel<double>() : batch_kernel<float>();
   const size_t smem = precision == MX_FP64 ? mx::bt_smem_bytes<double>() : mx::bt_smem_bytes<float>();
@@ -488,6 +504,7 @@ void mx_batch_destroy(mx_batch* b) {
   if (b->d_inst) cudaFree(b->d_inst);
   if (b->cpart) cudaFree(b->cpart);
   if (b->segpart) cudaFree(b->segpart);
+  if (b->qk) cudaFree(b->qk);
   if (b->bar) cudaFree(b->bar);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;

@@ -41,6 +41,13 @@ struct BInst {
   int every;         // record every `every` steps (0: none)
 };
 
+// Per table entry of an FP32 batch, what does not change with t: hk = (0.5 c) |k| and |k|, |k|^2
+// (coef_from_hk), so that phase A takes no FP64 square root.
+struct QK {
+  double hk;
+  float kabs, k2;
+};
+
 struct BatchArgs {
   const BInst* inst;
   int ninst;
@@ -50,6 +57,7 @@ struct BatchArgs {
   unsigned total_segs;
   void* cpart;     // [total_chunks][BT_CWARPS][16] of T: per-warp partial sums of a chunk (value 15: 0)
   double* segpart; // [2][total_segs][NSUM]: sums of BT_SEGC consecutive chunks
+  const QK* qk;    // [total_q] (FP32 batches; nullptr: coefficients from |k|^2 alone)
   unsigned* bar;  // [0] arrivals, [1] generation, [2] error flag
 };
 
@@ -251,9 +259,21 @@ __global__ void __maxnreg__(112) k_batch_steps(BatchArgs a) {
         const int ii = find_inst(a.inst, a.ninst, q, false);
         const BInst& b = a.inst[ii];
         const unsigned qi = q - b.q0;
-        if (b.tab && qi < (unsigned)b.nq)
-          reinterpret_cast<Coef<T>*>(b.tab)[qi] =
-              coef_direct<T, Coef<T>>(b.g.s0 * (double)qi, b.t0 + (double)n * b.h, b.g);
+        if (b.tab && qi < (unsigned)b.nq) {
+          const double t = b.t0 + (double)n * b.h;
+          Coef<T> v;
+          if constexpr (sizeof(T) == 4) {
+            if (a.qk) {
+              const QK e = a.qk[q];
+              v = coef_from_hk(e.hk, e.kabs, e.k2, qi == 0, t, b.g);
+            } else {
+              v = coef_direct<T, Coef<T>>(b.g.s0 * (double)qi, t, b.g);
+            }
+          } else {
+            v = coef_direct<T, Coef<T>>(b.g.s0 * (double)qi, t, b.g);
+          }
+          reinterpret_cast<Coef<T>*>(b.tab)[qi] = v;
+        }
       }
     }
     if (n >= 2 && n - 1 <= a.nsteps) batch_segments<T>(a, n - 1, a.segpart + (size_t)((n - 1) & 1) * a.total_segs * NSUM);

@@ -154,17 +154,24 @@ template <typename T, typename CoefT> __device__ __forceinline__ CoefT coef_dire
 // FP32, which gives the FP32 coefficients to a few FP32 ulps:
 //   cos th = 1 - 2 sin^2(th/2), sin th = 2 sin(th/2) cos(th/2),
 //   (1 - cos th)/|k|^2 = 2 sin^2(th/2) / |k|^2.
-template <> __device__ __forceinline__ Coef<float> coef_direct<float, Coef<float>>(double k2, double t, const GridParams& g) {
-  if (k2 == 0.0) return Coef<float>{1.f, 0.f, 0.f, 0.f};
-  const double kabs = sqrt(k2);
-  const double hp = 0.5 * g.c * kabs * t;
+// The same from hk = (0.5 c) |k| and |k|, |k|^2 in FP32 (zero: k = 0), for tables recomputed every
+// step from precomputed hk: the operations past the square root, in the same order.
+__device__ __forceinline__ Coef<float> coef_from_hk(double hk, float kabsf, float k2f, bool zero, double t,
+                                                    const GridParams& g) {
+  if (zero) return Coef<float>{1.f, 0.f, 0.f, 0.f};
+  const double hp = hk * t;
   const double n = rint(hp * 0.15915494309189533577);  // 1 / (2 pi)
   const double r = fma(-n, 2.4492935982947064e-16, fma(-n, 6.283185307179586, hp));
   float sh, ch;
   sincosf((float)r, &sh, &ch);
   const float s = 2.f * sh * ch, sh2 = sh * sh;
-  const float b = s / (float)kabs;
-  return Coef<float>{1.f - 2.f * sh2, 2.f * sh2 / (float)k2, b * (float)g.zh, b * (float)g.ze};
+  const float b = s / kabsf;
+  return Coef<float>{1.f - 2.f * sh2, 2.f * sh2 / k2f, b * (float)g.zh, b * (float)g.ze};
+}
+template <> __device__ __forceinline__ Coef<float> coef_direct<float, Coef<float>>(double k2, double t, const GridParams& g) {
+  if (k2 == 0.0) return Coef<float>{1.f, 0.f, 0.f, 0.f};
+  const double kabs = sqrt(k2);
+  return coef_from_hk(0.5 * g.c * kabs, (float)kabs, (float)k2, false, t, g);
 }
 template <> __device__ __forceinline__ Coef<double> coef_direct<double, Coef<double>>(double k2, double t, const GridParams& g) {
   if (k2 == 0.0) return Coef<double>{1.0, 0.0, 0.0, 0.0};
