@@ -191,7 +191,7 @@ KERNEL_NAMES = {
              "tensor-copy variant as scheduled; forward and inverse launches)",
     "z_fft": "k_fft_strided (z-direction, six components)",
     "z_fused": "k_z_fused_tma (z forward + exponential update + invariants + z inverse, tensor-copy prefetch)",
-    "spectral": "k_spectral_tma (exponential update + invariants)",
+    "spectral": "k_spectral_grp / k_spectral_tma (exponential update + invariants; rows sharing |k|^2 grouped when Mx is a multiple of 128)",
 }
 KERNEL_SOURCES = {
     "x_r2c": ["mx_fft.cuh", "mx_tma.cuh", "mx_kernels.cuh", "mx_xpass_tma.cuh", "mx_fft_launch.cuh", "mx_fft_f32.cu"],

@@ -68,6 +68,22 @@ static cudaError_t tma_mode(const float2* src, float2* dst, long npts, const Gri
   return cudaGetLastError();
 }
 
+// Grouped rows (k_spectral_grp): even ny and nz, so that rows y and -y (z and -z) share |k|^2;
+// Mx a multiple of GRP_L.
+template <bool INV>
+static cudaError_t grp_mode(const float2* src, float2* dst, long npts, const GridParams& g, const void* tab, int blocks,
+                            double* partials, unsigned* counter, double* record, cudaStream_t s) {
+  auto k = k_spectral_grp<INV>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k<<<blocks, TMA_THREADS, tma_smem_bytes(), s>>>(src, dst, npts, g, (const Coef<float>*)tab, partials, counter, record);
+  return cudaGetLastError();
+}
+
 template <>
 cudaError_t launch_spectral<float>(int mode, int coef_kind, const float2* src, float2* dst, long npts, const GridParams& g,
                                    const void* tab, double t, int blocks, double* partials, unsigned* counter,
@@ -75,6 +91,12 @@ cudaError_t launch_spectral<float>(int mode, int coef_kind, const float2* src, f
   // bulk-copy pipeline: table coefficients, even rows, 16-byte aligned buffers
   const bool aligned = (((uintptr_t)src | (uintptr_t)dst) & 15u) == 0;
   if (coef_kind == 0 && g.mx % 2 == 0 && aligned && npts < (1L << 31) && npts >= TMA_CH) {
+    // the updating modes take the table entries once per group of rows that share them (rows of
+    // whole segments, so that no consumer idles)
+    if (g.ny % 2 == 0 && g.nz % 2 == 0 && g.mx % GRP_L == 0) {
+      if (mode == 1) return grp_mode<false>(src, dst, npts, g, tab, blocks, partials, counter, record, s);
+      if (mode == 2) return grp_mode<true>(src, dst, npts, g, tab, blocks, partials, counter, record, s);
+    }
     switch (mode) {
       case 0: return tma_mode<false, true>(src, dst, npts, g, tab, blocks, partials, counter, record, s);
       case 1: return tma_mode<true, false>(src, dst, npts, g, tab, blocks, partials, counter, record, s);
