@@ -234,6 +234,20 @@ __host__ __device__ constexpr int num_stages(int N, int E) {
   }
   return s;
 }
+// Radix of the plan's last stage.
+__host__ __device__ constexpr int last_radix(int N, int E) {
+  int rem = N, r = 0;
+  while (rem > 1) {
+    r = pick_radix(rem, E);
+    rem /= r;
+  }
+  return r;
+}
+// A mirrored last stage (lines_fft MIRROR) needs two butterflies per thread there and an exchange
+// before it.
+__host__ __device__ constexpr bool mirror_ok(int N, int E) {
+  return num_stages(N, E) >= 2 && last_radix(N, E) > 0 && E / last_radix(N, E) == 2;
+}
 
 // Stage-major twiddle table of a line FFT of length N with E values per thread:
 // for each stage after the first (NS > 1, radix R) the entries
@@ -320,7 +334,12 @@ __host__ __device__ constexpr int line_bar(int P, int wide) { return (P <= 32 &&
 // a barrier has passed since sm was last read.
 // CNS > 1: the twiddles of the stage with NS == CNS come from twr (tw_cached),
 // in registers, instead of tw.
-template <typename T, int N, int E, int DIR, int NBAR, int NL, int NS = 1, int IX = 0, bool PP = false, int CNS = 0>
+// MIRROR (mirror_ok(N, E)): in the last stage thread t takes the butterflies t and
+// (t ? 2P - t : P) instead of t and t + P, so that the output k = j + NS r of register
+// b + 2 r has its mirror N - k in the same thread, at register E - 1 - m (m = b + 2 r; thread 0:
+// (E - m) mod E).  A real-input transform then pairs X_k with X_{N-k} without an exchange.
+template <typename T, int N, int E, int DIR, int NBAR, int NL, int NS = 1, int IX = 0, bool PP = false, int CNS = 0,
+          bool MIRROR = false>
 __device__ __forceinline__ void lines_fft(cx<T> (*v)[E], cx<T>* sm, int SS, int LS, int t, const twv<T>* tw,
                                           cx<T>* sm2 = nullptr, const twv<T>* twr = nullptr) {
   if constexpr (NS < N) {
@@ -328,9 +347,11 @@ __device__ __forceinline__ void lines_fft(cx<T> (*v)[E], cx<T>* sm, int SS, int 
     constexpr int R = pick_radix(N / NS, E);
     static_assert(R > 0, "no factorisation for this (N, E)");
     constexpr int B = E / R;  // butterflies per thread and line
+    constexpr bool MLAST = MIRROR && NS * R == N;  // this stage is the mirrored last one
+    static_assert(!MIRROR || (mirror_ok(N, E) && CNS == 0), "mirrored last stage: two butterflies per thread");
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-      const int j = t + P * b;
+      const int j = (MLAST && b == 1) ? (t ? 2 * P - t : P) : t + P * b;
       const int k = j % NS;
       if constexpr (NS > 1) {
         constexpr int OFF = tw_stage_off(N, E, NS);
@@ -362,8 +383,14 @@ __device__ __forceinline__ void lines_fft(cx<T> (*v)[E], cx<T>* sm, int SS, int 
 #pragma unroll
       for (int l = 0; l < NL; ++l)
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[l][m] = xb[l * LS + xoff(t + P * m, SS)];
-      lines_fft<T, N, E, DIR, NBAR, NL, NS * R, IX + 1, PP, CNS>(v, sm, SS, LS, t, tw, sm2, twr);
+        for (int m = 0; m < E; ++m) {
+          // the inputs of butterfly j of the next stage are j + (N / R') r'; mirrored when it is last
+          constexpr int R2 = pick_radix(N / (NS * R), E);
+          constexpr bool NEXT_M = MIRROR && NS * R * R2 == N;
+          const int e = NEXT_M ? ((m & 1) ? (t ? 2 * P - t : P) : t) + (N / R2) * (m >> 1) : t + P * m;
+          v[l][m] = xb[l * LS + xoff(e, SS)];
+        }
+      lines_fft<T, N, E, DIR, NBAR, NL, NS * R, IX + 1, PP, CNS, MIRROR>(v, sm, SS, LS, t, tw, sm2, twr);
     }
   }
 }

@@ -124,12 +124,22 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_r2c_tma(const T* __rest
     }
     fence_proxy_async_smem();
     mbar_arrive(&L.empty[s]);
-    lines_fft<T, M, E, -1, LB, 2>(v, line, 1, LS, t, tw + M);
-    // Z_{M-k} of position k = t + P m: for t > 0 it is register E-1-m of thread P - t,
-    // for t = 0 register (E - m) mod E of this thread.  Lines within a warp fetch it
+    // MIR: the last stage mirrored (lines_fft MIRROR), so that Z_{M-k} is this thread's own
+    // register E-1-m ((E - m) mod E for t = 0) and register m holds position
+    // k = (m odd ? (t ? 2P - t : P) : t) + 2P (m / 2)
+    constexpr bool MIR = mirror_ok(M, E);
+    lines_fft<T, M, E, -1, LB, 2, 1, 0, false, 0, MIR>(v, line, 1, LS, t, tw + M);
+    auto pos = [&](int m) { return MIR ? ((m & 1) ? (t ? 2 * P - t : P) : t) + 2 * P * (m >> 1) : t + P * m; };
+    // Otherwise Z_{M-k} of position k = t + P m: for t > 0 it is register E-1-m of thread
+    // P - t, for t = 0 register (E - m) mod E of this thread.  Lines within a warp fetch it
     // with a shuffle, wider lines through the line buffer.
     C zq[2][E];
-    if constexpr (LB < 0) {
+    if constexpr (MIR) {
+#pragma unroll
+      for (int l = 0; l < 2; ++l)
+#pragma unroll
+        for (int m = 0; m < E; ++m) zq[l][m] = t == 0 ? v[l][(E - m) % E] : v[l][E - 1 - m];
+    } else if constexpr (LB < 0) {
       const int lane = threadIdx.x & 31;
       const int src = (lane & ~(P - 1)) | ((P - t) & (P - 1));
 #pragma unroll
@@ -163,7 +173,7 @@ __global__ void __launch_bounds__((M / E) * TY + 32) k_x_r2c_tma(const T* __rest
         C* dst = out + row * M;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-          const int k = t + P * m;
+          const int k = pos(m);
           const C z = v[l][m];
           C r;
           if (k == 0) {
